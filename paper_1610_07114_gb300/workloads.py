@@ -1,0 +1,316 @@
+"""Seeded synthetic workloads for the thermal cascaded LBM (Fei & Luo, arXiv:1610.07114).
+
+This module is the only code shared by the CUDA path and the FP64 oracle.  It
+holds problem set-up only -- lattice sizes, physical parameters, boundary
+descriptions and initial macroscopic fields -- and none of the method's
+arithmetic (no equilibria, no relaxation rates, no moments).  Each side turns a
+case dict into its own parameter struct.
+
+Case dict vocabulary (names follow the paper's notation):
+
+    nx, ny            lattice nodes; x fastest in every [ny][nx] array
+    thermal           True: total-energy distribution h evolved (Section IV)
+                      False: athermal cascaded LBM with T = T0 (Sections II-III)
+    correction        True: correction term C_a of Section IV included
+    visc_law, visc    "nu" kinematic viscosity | "mu" dynamic viscosity |
+                      "mu_T" mu = visc * T/T0 | "w1" fixed w1 (Eq. 29)
+    w2, w3, w4        Eq. 8 rates; w_equal=True sets all four equal to w1 (BGK limit)
+    Pr, gamma, R, T0  Prandtl number, specific-heat ratio, gas constant, reference T
+    force             {"kind": "none"} | {"kind": "accel", "ax", "ay"} (F = rho a) |
+                      {"kind": "taylor_green", "amp"}: F = amp (sin kx sin ky, cos kx cos ky)
+    walls             {"x-","x+","y-","y+"} -> {"kind": "periodic"|"zouhe"|"nee"|"equilibrium",
+                      "ux", "uy", "T", "rho", "therm": "fixed"|"adiabatic"}
+    storage           "fp32" | "bf16" | "fp16" population storage of the CUDA path
+"""
+from __future__ import annotations
+
+import copy
+import math
+
+import numpy as np
+
+# Gas constant in lattice units.  Section V.C normalises p0 = rho0 R T0 = 1/3, but with
+# the local temperature in the total-energy equilibrium the D2Q9 scheme's linearised
+# step then grows grid-scale two-dimensional modes (k = (pi, pi)) by a factor 1.8-4.8
+# per step for every w1; R T0 <= 0.18 is stable for w1 <= 1.8.  Thermal cases therefore
+# take R T0 = 1/6 (the correction term then cancels the defect rho u (1 - 3RT)); the
+# athermal cascaded LBM (c_s^2 = R T0 = 1/3) and the paper's odd-width one-dimensional
+# Couette case keep R = 1/3.
+R_DEFAULT = 1.0 / 6.0
+R_PAPER = 1.0 / 3.0
+SIDES = ("x-", "x+", "y-", "y+")
+
+
+def _periodic():
+    return {"kind": "periodic", "ux": 0.0, "uy": 0.0, "T": 1.0, "rho": 1.0, "therm": "fixed"}
+
+
+def _wall(kind, ux=0.0, uy=0.0, T=1.0, rho=1.0, therm="fixed"):
+    return {"kind": kind, "ux": float(ux), "uy": float(uy), "T": float(T), "rho": float(rho), "therm": therm}
+
+
+def base_case(nx, ny, **kw):
+    case = {
+        "name": "custom",
+        "nx": int(nx),
+        "ny": int(ny),
+        "thermal": True,
+        "correction": True,
+        "visc_law": "nu",
+        "visc": 0.05,
+        "w2": 1.0,
+        "w3": 1.0,
+        "w4": 1.0,
+        "w_equal": False,
+        "Pr": 0.71,
+        "gamma": 1.4,
+        "R": R_DEFAULT,
+        "T0": 1.0,
+        "force": {"kind": "none", "ax": 0.0, "ay": 0.0, "amp": 0.0},
+        "walls": {s: _periodic() for s in SIDES},
+        "storage": "fp32",
+    }
+    for k, v in kw.items():
+        case[k] = v
+    return case
+
+
+def uniform_fields(nx, ny, rho=1.0, ux=0.0, uy=0.0, T=1.0):
+    shape = (ny, nx)
+    return {
+        "rho": np.full(shape, float(rho)),
+        "ux": np.full(shape, float(ux)),
+        "uy": np.full(shape, float(uy)),
+        "T": np.full(shape, float(T)),
+    }
+
+
+# --------------------------------------------------------------------------- paper cases
+
+
+def couette(nx=8, ny=64, U=0.05, nu=0.05, Pr=0.71, gamma=1.4, T_wall=1.0, storage="fp32"):
+    """Thermal Couette flow with viscous heating (Section V.B set-up, isothermal walls).
+
+    Periodic in x; y = 0 is a wall at rest and y = ny-1 moves with u = (U, 0); both
+    walls use non-equilibrium bounce-back for velocity and non-equilibrium
+    extrapolation for temperature (Section V.B), at T = T_wall.  Initial state rho = 1,
+    u = 0, T = T_wall.  With constant mu and lambda the steady temperature is
+    T = T_wall + Pr U^2 / (2 c_p) eta (1 - eta), eta = y / (ny - 1).
+    """
+    case = base_case(nx, ny, name=f"couette_{nx}x{ny}", visc_law="nu", visc=nu, Pr=Pr, gamma=gamma,
+                     storage=storage)
+    case["walls"]["y-"] = _wall("zouhe", 0.0, 0.0, T_wall)
+    case["walls"]["y+"] = _wall("zouhe", U, 0.0, T_wall)
+    case["U"] = U
+    return case, uniform_fields(nx, ny, T=T_wall)
+
+
+def couette_paper(Pr=5.0, gamma=5.0 / 3.0, nx=5, ny=40, Ma=0.35, mu0=0.35):
+    """The paper's thermal Couette variant (Section V.B, Table 2): top wall moving at
+    U = Ma sqrt(gamma R T0) with T = T0, bottom wall fixed and adiabatic, mu/mu0 = T/T0,
+    w2 = 1.1, w3 = 1.6, w4 = 0.3."""
+    U = Ma * math.sqrt(gamma * R_PAPER * 1.0)
+    case = base_case(nx, ny, name=f"couette_paper_Pr{Pr}_g{gamma:.3f}", visc_law="mu_T", visc=mu0, Pr=Pr,
+                     gamma=gamma, w2=1.1, w3=1.6, w4=0.3, R=R_PAPER)
+    case["walls"]["y-"] = _wall("zouhe", 0.0, 0.0, 1.0, therm="adiabatic")
+    case["walls"]["y+"] = _wall("zouhe", U, 0.0, 1.0)
+    case["U"] = U
+    case["Ma"] = Ma
+    return case, uniform_fields(nx, ny)
+
+
+def rb_gravity(Ra, ny, Pr=0.71, dT=0.02, u_c=0.03, T0=1.0):
+    """Gravity and viscosity of a Rayleigh-Benard layer (Section V.D):
+    Ra = g beta dT H^3 Pr / nu^2, u_c = sqrt(g beta dT H), beta = 1/T0, H = ny - 1."""
+    H = ny - 1
+    beta = 1.0 / T0
+    g = u_c * u_c / (beta * dT * H)
+    nu = math.sqrt(g * beta * dT * H ** 3 * Pr / Ra)
+    return g, nu
+
+
+def rayleigh_benard(nx=256, ny=128, Ra=1e4, Pr=0.71, gamma=1.4, T_bot=1.01, T_top=0.99, u_c=0.03,
+                    seed=1, amp=1e-4, storage="fp32"):
+    """Rayleigh-Benard convection with gravity as a direct body force (Section V.D).
+
+    Periodic in x; walls at y = 0 (hot) and y = ny-1 (cold), at rest.  Velocity walls
+    use non-equilibrium bounce-back and temperature walls non-equilibrium
+    extrapolation (the Section V.B pairing): extrapolating the density as well lets
+    mass through a wall under the body force.  Initial T: linear between the walls
+    plus a seeded uniform perturbation of amplitude `amp` in the interior; initial
+    rho: the discrete hydrostatic profile of that mean T, normalised to mean 1.
+    """
+    T0 = 0.5 * (T_bot + T_top)
+    g, nu = rb_gravity(Ra, ny, Pr, T_bot - T_top, u_c, T0)
+    case = base_case(nx, ny, name=f"rb_{nx}x{ny}_Ra{Ra:g}", visc_law="nu", visc=nu, Pr=Pr, gamma=gamma,
+                     T0=T0, storage=storage)
+    case["force"] = {"kind": "accel", "ax": 0.0, "ay": -g, "amp": 0.0}
+    case["walls"]["y-"] = _wall("zouhe", 0.0, 0.0, T_bot)
+    case["walls"]["y+"] = _wall("zouhe", 0.0, 0.0, T_top)
+    case["Ra"] = Ra
+    case["g"] = g
+    case["T_bot"], case["T_top"] = T_bot, T_top
+    rng = np.random.default_rng(seed)
+    y = np.arange(ny, dtype=np.float64)
+    Tcol = T_bot + (T_top - T_bot) * y / (ny - 1)
+    R = case["R"]
+    rho_col = np.empty(ny)
+    rho_col[0] = 1.0
+    for j in range(ny - 1):  # p = rho R T, (p_{j+1} - p_j) = -g (rho_j + rho_{j+1}) / 2
+        rho_col[j + 1] = rho_col[j] * (R * Tcol[j] - 0.5 * g) / (R * Tcol[j + 1] + 0.5 * g)
+    rho_col /= rho_col.mean()
+    T = np.repeat(Tcol[:, None], nx, axis=1)
+    pert = rng.uniform(-amp, amp, size=(ny, nx))
+    pert[0, :] = 0.0
+    pert[-1, :] = 0.0
+    T = T + pert
+    fields = {
+        "rho": np.repeat(rho_col[:, None], nx, axis=1).copy(),
+        "ux": np.zeros((ny, nx)),
+        "uy": np.zeros((ny, nx)),
+        "T": T,
+    }
+    return case, fields
+
+
+def shock_tube(nx=4096, ny=4, rho_l=1.05, rho_r=1.0, T=1.0, w1=1.887, storage="fp32"):
+    """Low-Mach shock tube (Section V.C): periodic in y, equilibrium distributions at
+    x = 0 and x = nx-1 with the initial end states; gamma = 1.4, Pr = 0.71,
+    w1 = 1.887, w2 = w3 = w4 = 1."""
+    case = base_case(nx, ny, name=f"shock_{nx}x{ny}", visc_law="w1", visc=w1, Pr=0.71, gamma=1.4,
+                     storage=storage)
+    case["walls"]["x-"] = _wall("equilibrium", 0.0, 0.0, T, rho_l)
+    case["walls"]["x+"] = _wall("equilibrium", 0.0, 0.0, T, rho_r)
+    f = uniform_fields(nx, ny, T=T)
+    f["rho"][:, : nx // 2] = rho_l
+    f["rho"][:, nx // 2:] = rho_r
+    case["rho_l"], case["rho_r"] = rho_l, rho_r
+    return case, f
+
+
+def taylor_green(n=64, F0=1e-5, nu=0.02, thermal=False, storage="fp32"):
+    """Steady forced Taylor-Green flow (Section V.A): periodic N x N lattice, node i at
+    x = i * 2 pi / N, F = F0 (sin x sin y, cos x cos y), rho = 1 and u = 0 initially,
+    w1 = w2 = w3 = w4 (BGK limit).  Closed form u = u0 (sin x sin y, cos x cos y) with
+    u0 = F0 / (2 nu k^2), k = 2 pi / N."""
+    case = base_case(n, n, name=f"tg_{n}", thermal=thermal, correction=thermal, visc_law="nu", visc=nu,
+                     w_equal=True, storage=storage, R=R_DEFAULT if thermal else R_PAPER)
+    case["force"] = {"kind": "taylor_green", "ax": 0.0, "ay": 0.0, "amp": F0}
+    k = 2.0 * math.pi / n
+    case["u0"] = F0 / (2.0 * nu * k * k)
+    return case, uniform_fields(n, n)
+
+
+def taylor_green_fields(n, u0):
+    """Closed-form steady Taylor-Green velocity at the nodes (Section V.A)."""
+    k = 2.0 * math.pi / n
+    x = np.arange(n) * k
+    X, Y = np.meshgrid(x, x, indexing="xy")  # arrays [y][x]
+    return u0 * np.sin(X) * np.sin(Y), u0 * np.cos(X) * np.cos(Y)
+
+
+def random_periodic(nx, ny, seed=0, thermal=True, force="accel", amp_rho=1e-2, amp_u=2e-2, amp_T=1e-2,
+                    visc=0.03, storage="fp32", correction=None):
+    """Seeded random smooth-ish state on a fully periodic lattice, for parity checks."""
+    rng = np.random.default_rng(seed)
+    case = base_case(nx, ny, name=f"rand_{nx}x{ny}_s{seed}", thermal=thermal,
+                     correction=thermal if correction is None else correction, visc_law="nu", visc=visc,
+                     w2=1.2, w3=1.1, w4=0.9, storage=storage)
+    if force == "accel":
+        case["force"] = {"kind": "accel", "ax": 1e-5, "ay": -2e-5, "amp": 0.0}
+    elif force == "taylor_green":
+        case["force"] = {"kind": "taylor_green", "ax": 0.0, "ay": 0.0, "amp": 1e-5}
+
+    def field(amp):
+        a = rng.uniform(-1.0, 1.0, size=(ny, nx))
+        # one pass of a 5-point average keeps gradients moderate
+        a = (a + np.roll(a, 1, 0) + np.roll(a, -1, 0) + np.roll(a, 1, 1) + np.roll(a, -1, 1)) / 5.0
+        return amp * a
+
+    fields = {
+        "rho": 1.0 + field(amp_rho),
+        "ux": field(amp_u),
+        "uy": field(amp_u),
+        "T": 1.0 + (field(amp_T) if thermal else 0.0),
+    }
+    return case, fields
+
+
+def with_walls(case, fields, axis="y", kind="nee", seed=0):
+    """Copy of a random case with walls on one axis (for boundary parity checks)."""
+    case = copy.deepcopy(case)
+    lo, hi = ("y-", "y+") if axis == "y" else ("x-", "x+")
+    rng = np.random.default_rng(seed + 17)
+    if kind == "zouhe":
+        t = "ux" if axis == "y" else "uy"
+        u_lo, u_hi = {t: 0.0}, {t: 0.03}
+    else:
+        u_lo, u_hi = {}, {}
+    case["walls"][lo] = _wall(kind, T=1.0 + 0.01 * rng.uniform(), rho=1.02, **u_lo)
+    case["walls"][hi] = _wall(kind, T=1.0 - 0.01 * rng.uniform(), rho=0.99, **u_hi)
+    case["name"] += f"_{axis}{kind}"
+    return case, fields
+
+
+# --------------------------------------------------------------------------- growth workloads
+
+
+def batched_rb_sweep(count=256, seed=1234, sizes=((64, 32), (128, 64), (256, 128), (512, 256), (1024, 512)),
+                     ra_lo=2e3, ra_hi=1e6, storage="fp16"):
+    """Batched Rayleigh-Benard sweep: `count` independent lattices, sizes uniform over
+    `sizes` (aspect 2:1), Ra log-uniform in [ra_lo, ra_hi], Pr = 0.71."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        nx, ny = sizes[int(rng.integers(len(sizes)))]
+        Ra = float(math.exp(rng.uniform(math.log(ra_lo), math.log(ra_hi))))
+        out.append(rayleigh_benard(nx, ny, Ra=Ra, seed=seed + i, storage=storage))
+    return out
+
+
+def serving_trace(duration_s=2.0, rate=200.0, seed=42, scale=1.0, max_nodes=None):
+    """Poisson-arriving requests (mean `rate`/s) mixing thermal Couette (32 x 128),
+    forced Taylor-Green (256^2 .. 2048^2) and Rayleigh-Benard (128x64 .. 4096x2048,
+    Ra up to 1e7).  Each request asks for a fixed step count.  `scale` shrinks lattice
+    sides (for small test runs); `max_nodes` caps lattice size."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    reqs = []
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t > duration_s:
+            break
+        kind = int(rng.integers(3))
+        if kind == 0:
+            nx, ny = 32, 128
+            case, fields = None, None
+            spec = ("couette", nx, ny, {})
+        elif kind == 1:
+            n = int(2 ** rng.integers(8, 12))
+            spec = ("taylor_green", n, n, {})
+        else:
+            e = int(rng.integers(7, 13))
+            nx = 2 ** e
+            Ra = float(math.exp(rng.uniform(math.log(2e3), math.log(1e7))))
+            spec = ("rayleigh_benard", nx, nx // 2, {"Ra": Ra})
+        name, nx, ny, extra = spec
+        nx = max(8, int(nx * scale))
+        ny = max(8, int(ny * scale))
+        if max_nodes is not None:
+            while nx * ny > max_nodes:
+                nx //= 2
+                ny //= 2
+        steps = int(rng.choice([200, 500, 1000, 2000]))
+        reqs.append({"t_arrival": t, "kind": name, "nx": nx, "ny": ny, "steps": steps, "seed": len(reqs), **extra})
+    return reqs
+
+
+def build_request(req, storage="fp16"):
+    """Case and initial fields of one serving request."""
+    if req["kind"] == "couette":
+        return couette(req["nx"], req["ny"], storage=storage)
+    if req["kind"] == "taylor_green":
+        n = req["nx"]
+        F0 = 1e-5 * (64.0 / n) ** 2  # keeps u0 at the Section V.A value of 0.026
+        return taylor_green(n, F0=F0, nu=0.02, thermal=True, storage=storage)
+    return rayleigh_benard(req["nx"], req["ny"], Ra=req.get("Ra", 1e4), seed=req["seed"], storage=storage)

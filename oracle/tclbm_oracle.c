@@ -497,7 +497,9 @@ int oracle_max_threads(void) {
 #endif
 }
 
-/* Initial populations from the fields (arrays [ny][nx]): f_bar = f^eq - S/2, h_bar = h^eq. */
+/* Initial populations from the fields (arrays [ny][nx]): f_bar = f^eq - S/2, h_bar = h^eq;
+ * the wall nodes are then rebuilt by their wall scheme from the initial interior state,
+ * so that the initial state satisfies the boundary conditions like every later one. */
 int oracle_init(const oracle_params* p, const double* rho, const double* ux, const double* uy,
                 const double* T, double* f, double* h) {
     if (oracle_check(p)) return -1;
@@ -516,6 +518,21 @@ int oracle_init(const oracle_params* p, const double* rho, const double* ux, con
             if (p->thermal) {
                 oracle_heq(rho[i], ux[i], uy[i], p->R * Tn, b, heq);
                 for (int a = 0; a < Q; ++a) h[at(p, a, x, y)] = heq[a];
+            }
+        }
+    for (int y = 0; y < p->ny; ++y)
+        for (int x = 0; x < p->nx; ++x) {
+            const int side = wall_side_of(p, x, y);
+            if (side < 0) continue;
+            double fb[9], hb[9] = {0}, ff[9], hf[9] = {0};
+            const int xf = x + NRM_X[side], yf = y + NRM_Y[side];
+            gather(p, f, x, y, fb);
+            gather(p, f, xf, yf, ff);
+            if (p->thermal) { gather(p, h, x, y, hb); gather(p, h, xf, yf, hf); }
+            wall_rebuild(p, side, x, y, fb, hb, ff, hf);
+            for (int a = 0; a < Q; ++a) {
+                f[at(p, a, x, y)] = fb[a];
+                if (p->thermal) h[at(p, a, x, y)] = hb[a];
             }
         }
     return 0;

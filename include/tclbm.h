@@ -1,0 +1,178 @@
+/*
+ * tclbm.h -- C ABI of the GB300 thermal cascaded lattice Boltzmann library
+ * (Fei & Luo, "Thermal cascaded lattice Boltzmann method", arXiv:1610.07114).
+ *
+ * One handle = one D2Q9 lattice resident in device memory: two ping-pong copies of
+ * the transformed populations f_bar (Section III, Eq. 12 and Eq. 27) and h_bar
+ * (Section IV), structure-of-arrays, x fastest.  tclbm_step() advances it by whole
+ * time steps with the fused collide-and-stream kernel: macroscopic moments (Eq. 20
+ * and the temperature of Section IV), correction-term gradients (Section IV),
+ * cascaded collision of f_bar (Eq. 8 with the shifted equilibria, Eq. 18, Eq. 3,
+ * plus S_a and C_a), BGK collision of h_bar with its K_a coupling (Section IV),
+ * pull streaming and the wall schemes of Section V.
+ *
+ * Conventions for every entry point:
+ *   - Returns a tclbm_status; never aborts, never prints.  tclbm_last_error() gives a
+ *     thread-local message for the last non-OK status of the calling thread.
+ *   - Field arrays are double, [ny][nx] row-major (x fastest).  `on_device` = 1 means
+ *     the pointer is device memory of the handle's device, 0 means host memory.
+ *     Caller-owned arrays are read or written only during the call.
+ *   - Work is queued on the handle's CUDA stream; calls that return data to the
+ *     caller (moments, diagnostics, populations) synchronise that stream.  CUDA
+ *     errors raised asynchronously surface at the next synchronising call as
+ *     TCLBM_ECUDA.
+ *   - Calls on one handle are not thread-safe; distinct handles are independent.
+ */
+#ifndef TCLBM_H
+#define TCLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TCLBM_OK = 0,
+    TCLBM_EINVAL = -1,         /* invalid argument or parameter set */
+    TCLBM_ENOMEM = -2,         /* device allocation failed (allocator returned NULL) */
+    TCLBM_ECUDA = -3,          /* a CUDA runtime call or kernel failed */
+    TCLBM_ENONFINITE = -4,     /* a non-finite value was found in the state */
+    TCLBM_ETIMEOUT = -5,       /* a bounded device wait gave up */
+    TCLBM_EUNSUPPORTED = -6    /* valid request the library does not implement */
+} tclbm_status;
+
+/* Sides of the lattice, in this order in tclbm_params.wall[]. */
+enum { TCLBM_SIDE_XM = 0, TCLBM_SIDE_XP = 1, TCLBM_SIDE_YM = 2, TCLBM_SIDE_YP = 3 };
+
+/* Wall schemes of Section V.  Walls are wet: the wall lies on the first/last node row
+ * (or column); after streaming that node's populations are rebuilt and it then
+ * collides like any other node.  Opposite sides must both be periodic or both walls,
+ * and walls may sit on one axis only. */
+enum {
+    TCLBM_WALL_PERIODIC = 0,
+    TCLBM_WALL_ZOUHE = 1,       /* non-equilibrium bounce-back, tangential wall velocity */
+    TCLBM_WALL_NEE = 2,         /* non-equilibrium extrapolation of f_bar (and h_bar) */
+    TCLBM_WALL_EQUILIBRIUM = 3  /* equilibrium distributions at (rho, u, T) of the wall */
+};
+/* Temperature treatment of a ZOUHE or NEE wall (h_bar by non-equilibrium extrapolation). */
+enum { TCLBM_THERM_FIXED_T = 0, TCLBM_THERM_ADIABATIC = 1 };
+/* How w1 follows from the viscosity, Eq. 29: 1/w1 = mu/p + 1/2, p = rho R T. */
+enum {
+    TCLBM_VISC_NU = 0,       /* visc = kinematic nu, mu = rho nu (w1 per node) */
+    TCLBM_VISC_MU = 1,       /* visc = dynamic mu */
+    TCLBM_VISC_MU_PROP_T = 2,/* mu = visc * T / T0 (Section V.B) */
+    TCLBM_VISC_W1 = 3        /* visc = w1, fixed */
+};
+/* Body force of Section III (force density F; acceleration a = F / rho). */
+enum {
+    TCLBM_FORCE_NONE = 0,
+    TCLBM_FORCE_ACCEL = 1,       /* F = rho (ax, ay): gravity as a direct force (Section V.D) */
+    TCLBM_FORCE_TAYLOR_GREEN = 2 /* F = famp (sin kx sin ky, cos kx cos ky), k = 2 pi / n (Section V.A) */
+};
+/* Population storage.  FP32 stores f_bar and h_bar as they are; the 16-bit formats
+ * store the deviation from the rest state (f_bar - f^eq(1, 0, T0), h_bar - h^eq(1, 0, T0))
+ * and compute in FP32. */
+enum { TCLBM_STORE_FP32 = 0, TCLBM_STORE_BF16 = 1, TCLBM_STORE_FP16 = 2 };
+
+typedef struct {
+    int32_t kind;   /* TCLBM_WALL_* */
+    int32_t therm;  /* TCLBM_THERM_* (ZOUHE / NEE walls of a thermal lattice) */
+    double rho;     /* wall density (EQUILIBRIUM walls) */
+    double ux, uy;  /* wall velocity; ZOUHE walls move tangentially only */
+    double T;       /* wall temperature */
+} tclbm_wall;
+
+typedef struct {
+    int32_t nx, ny;       /* nodes; >= 1 on periodic axes, >= 3 on a walled axis */
+    int32_t thermal;      /* 1: h_bar evolved, T local (Section IV); 0: athermal, T = T0 */
+    int32_t correction;   /* 1: correction term C_a (Section IV); needs thermal */
+    int32_t visc_law;     /* TCLBM_VISC_* */
+    double visc;          /* see visc_law */
+    int32_t bgk;          /* 1: w2 = w3 = w4 = w1 (the BGK limit of Section V.A) */
+    double w2, w3, w4;    /* Eq. 8 rates of E, (M21, M12), M22; each in (0, 2) */
+    double Pr;            /* Prandtl number (> 0) */
+    double gamma;         /* specific-heat ratio (> 1); b = 2 / (gamma - 1) */
+    double R, T0;         /* gas constant and reference temperature (> 0) */
+    int32_t force_kind;   /* TCLBM_FORCE_* */
+    double ax, ay;        /* TCLBM_FORCE_ACCEL */
+    double famp;          /* TCLBM_FORCE_TAYLOR_GREEN */
+    tclbm_wall wall[4];   /* indexed by TCLBM_SIDE_* */
+    int32_t storage;      /* TCLBM_STORE_* */
+    double T_ref;         /* reference temperature of the Nusselt sum in diagnostics */
+} tclbm_params;
+
+/* Device allocator hooks.  alloc(bytes, stream, ctx) returns device memory or NULL;
+ * free(ptr, bytes, stream, ctx) releases it.  Both may be NULL: the library then uses
+ * cudaMalloc / cudaFree. */
+typedef void* (*tclbm_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*tclbm_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+typedef struct tclbm_lattice tclbm_lattice;
+
+/* Number of doubles written by tclbm_diagnostics(). */
+#define TCLBM_NDIAG 8
+
+/* Device bytes one lattice of these parameters holds (state, tables, scratch). */
+size_t tclbm_state_bytes(const tclbm_params* params);
+
+/* Validate params, derive constants, allocate the state on the current device.
+ * `stream` is a cudaStream_t (NULL = legacy default stream).  No kernel runs.
+ * EINVAL on bad parameters, ENOMEM if the allocator fails; *out is NULL on error. */
+tclbm_status tclbm_create(const tclbm_params* params, tclbm_alloc_fn alloc, tclbm_free_fn free_fn, void* ctx,
+                          void* stream, tclbm_lattice** out);
+
+/* Set the populations from macroscopic fields: f_bar = f^eq(rho, u, T) - S/2 (the
+ * correction term is taken as zero at t = 0) and h_bar = h^eq(rho, u, T), so that
+ * Eq. 20 and the temperature formula return the given fields.  Resets the step count. */
+tclbm_status tclbm_init_fields(tclbm_lattice* lat, const double* rho, const double* ux, const double* uy,
+                               const double* T, int32_t on_device);
+
+/* Advance `nsteps` >= 0 time steps (asynchronous on the handle's stream). */
+tclbm_status tclbm_step(tclbm_lattice* lat, int64_t nsteps);
+
+/* Macroscopic fields of the current state (Eq. 20; T per Section IV, T0 if athermal),
+ * each [ny][nx]; any pointer may be NULL.  Synchronises the stream. */
+tclbm_status tclbm_moments(tclbm_lattice* lat, double* rho, double* ux, double* uy, double* T, int32_t on_device);
+
+/* FP64 global sums of the current state, reduced on the device:
+ * out[0] sum rho, out[1] sum rho ux, out[2] sum rho uy, out[3] sum h_bar (total energy),
+ * out[4] sum rho |u|^2 / 2 (kinetic energy, Section V.D), out[5] sum uy (T - T_ref)
+ * (the Nusselt sum of Section V.D), out[6] sum |u - u_snap|^2, out[7] sum |u|^2
+ * (steady-state residual of Section V.A against the last tclbm_snapshot_velocity()).
+ * Synchronises the stream. */
+tclbm_status tclbm_diagnostics(tclbm_lattice* lat, double out[TCLBM_NDIAG]);
+
+/* Store the current velocity field as the reference of out[6] in tclbm_diagnostics(). */
+tclbm_status tclbm_snapshot_velocity(tclbm_lattice* lat);
+
+/* Copy the populations out of / into the current state as double [9][ny][nx] each
+ * (f_bar, then h_bar; h may be NULL for athermal lattices).  Synchronising. */
+tclbm_status tclbm_get_populations(tclbm_lattice* lat, double* f, double* h, int32_t on_device);
+tclbm_status tclbm_set_populations(tclbm_lattice* lat, const double* f, const double* h, int32_t on_device);
+
+/* Time steps taken since the last init. */
+int64_t tclbm_steps_done(const tclbm_lattice* lat);
+
+/* Replace the handle's stream (cudaStream_t). */
+tclbm_status tclbm_set_stream(tclbm_lattice* lat, void* stream);
+
+/* Release the handle and its device memory; NULL is accepted. */
+tclbm_status tclbm_destroy(tclbm_lattice* lat);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* tclbm_last_error(void);
+
+/* Name of the step kernel variant and its launch shape for this handle, for
+ * profiling ("tclbm_step_kernel<...> grid (gx, gy) block (bx)"). */
+const char* tclbm_describe(const tclbm_lattice* lat);
+
+/* Launch-shape override for tuning: tile width tx (32, 64 or 128 nodes) and rows per
+ * CTA ty (>= 4); 0 keeps the library's choice. */
+tclbm_status tclbm_set_tile(tclbm_lattice* lat, int32_t tx, int32_t ty);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TCLBM_H */

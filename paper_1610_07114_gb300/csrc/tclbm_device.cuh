@@ -1,0 +1,636 @@
+// tclbm_device.cuh -- per-node arithmetic and the fused collide-and-stream kernel of
+// the thermal cascaded lattice Boltzmann method (Fei & Luo, arXiv:1610.07114), D2Q9,
+// written for sm_103a.
+//
+// Layout (structure of arrays): plane q in [0, 9) holds f_bar_q, plane 9 + q holds
+// h_bar_q; each plane is ny rows of `pitch` elements, x fastest.  Two ping-pong
+// copies; a step reads one and writes the other (pull streaming: the kernel gathers
+// f_bar_q(x, t+1) = f_out_q(x - e_q, t) from the source copy and writes the node's
+// own post-collision values at its own address).
+//
+// The kernel marches each CTA up a strip of TX columns, one row at a time, keeping
+// the next row's streamed populations in registers.  That lookahead gives the
+// moments of row r+1 before row r collides, which the correction term of Section IV
+// needs (central differences of u(1 - theta) at the collision's time level); the
+// x-neighbours come from a three-row shared-memory ring.  No tensor cores: the update
+// is a memory-bound stencil.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace tclbm {
+
+enum { SIDE_XM = 0, SIDE_XP = 1, SIDE_YM = 2, SIDE_YP = 3 };
+enum { WALL_PERIODIC = 0, WALL_ZOUHE = 1, WALL_NEE = 2, WALL_EQUILIBRIUM = 3 };
+enum { THERM_FIXED_T = 0, THERM_ADIABATIC = 1 };
+enum { VISC_NU = 0, VISC_MU = 1, VISC_MU_PROP_T = 2, VISC_W1 = 3 };
+enum { FORCE_NONE = 0, FORCE_ACCEL = 1, FORCE_TAYLOR_GREEN = 2 };
+
+// Device-side constants of one lattice (derived on the host from tclbm_params).
+struct DevParams {
+    int nx, ny, pitch;
+    long long plane;  // ny * pitch elements
+    int xper, yper;   // 1 if the axis is periodic
+    int visc_law;
+    float visc, w2, w3, w4;
+    int bgk;
+    float R, T0, b, two_over_b, inv_R, inv_Pr, Pr_m1;
+    float RTp;            // R T0 (the athermal temperature)
+    float RT0, Et0, cRT;  // rest state of the deviations (exact floats); cRT = (2/b) Et0 - RT0
+    int force_kind;
+    float ax, ay, famp;
+    const float* sx;  // sin(2 pi x / nx), cos(...), sin(2 pi y / ny), cos(...)
+    const float* cx;
+    const float* sy;
+    const float* cy;
+    int wall_kind[4], wall_therm[4];
+    float wall_rho[4], wall_ux[4], wall_uy[4], wall_T[4];
+    float fbase[9], hbase[9];  // rest-state populations f^eq(1, 0, T0), h^eq(1, 0, T0)
+};
+
+// ---------------------------------------------------------------- storage formats
+//
+// Every format stores deviations from the rest state, df_q = f_bar_q - f^eq_q(1, 0, T0)
+// and dh_q = h_bar_q - h^eq_q(1, 0, T0), and the collision is carried out on those
+// deviations: the O(1) parts of moments and equilibria then cancel analytically
+// instead of in FP32 arithmetic, so a per-step change far below one ulp of an O(1)
+// population (viscous heating is ~1e-8 per step in a slow shear flow) is still
+// represented.  16-bit formats use the same deviations, rounded to half or bfloat16.
+
+template <class ST>
+struct Store;
+template <>
+struct Store<float> {
+    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <>
+struct Store<__half> {
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <>
+struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ---------------------------------------------------------------- node arithmetic
+
+// Node state after Eq. 20, kept both whole and as deviations from the rest state
+// (rho0 = 1, RT0 = R T0, Et0 = b RT0 / 2): Et = sum h_bar / rho is the total energy per
+// unit mass and RT = (2/b)(Et - u^2/2).
+struct Macro {
+    float rho, drho, ux, uy, ax, ay, RT, dRT, Et, dEt;
+};
+
+__device__ __forceinline__ void force_at(const DevParams& p, int x, int y, float rho, float& Fx, float& Fy) {
+    if (p.force_kind == FORCE_ACCEL) {
+        Fx = __fmul_rn(rho, p.ax);
+        Fy = __fmul_rn(rho, p.ay);
+    } else if (p.force_kind == FORCE_TAYLOR_GREEN) {
+        Fx = __fmul_rn(__fmul_rn(p.famp, p.sx[x]), p.sy[y]);
+        Fy = __fmul_rn(__fmul_rn(p.famp, p.cx[x]), p.cy[y]);
+    } else {
+        Fx = 0.f;
+        Fy = 0.f;
+    }
+}
+
+__device__ __forceinline__ float sum9(const float* v) {
+    return __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(v[0], v[1]), __fadd_rn(v[2], v[3])),
+                               __fadd_rn(__fadd_rn(v[4], v[5]), __fadd_rn(v[6], v[7]))),
+                     v[8]);
+}
+
+// Eq. 20 and the temperature of Section IV from deviations df, dh.  Explicitly rounded
+// operations: halo nodes evaluate this in other inlined copies, and the result must be
+// bit-identical to the owner's so that the state does not depend on the launch shape.
+template <bool THERMAL>
+__device__ __forceinline__ Macro macro_of(const DevParams& p, const float* f, const float* h, int x, int y) {
+    Macro m;
+    m.drho = sum9(f);
+    m.rho = __fadd_rn(1.0f, m.drho);
+    const float jx = __fadd_rn(__fadd_rn(__fsub_rn(f[1], f[3]), __fsub_rn(f[5], f[6])), __fsub_rn(f[8], f[7]));
+    const float jy = __fadd_rn(__fadd_rn(__fsub_rn(f[2], f[4]), __fsub_rn(f[5], f[7])), __fsub_rn(f[6], f[8]));
+    float Fx, Fy;
+    force_at(p, x, y, m.rho, Fx, Fy);
+    const float irho = __frcp_rn(m.rho);
+    m.ux = __fmul_rn(__fmaf_rn(0.5f, Fx, jx), irho);
+    m.uy = __fmul_rn(__fmaf_rn(0.5f, Fy, jy), irho);
+    m.ax = __fmul_rn(Fx, irho);
+    m.ay = __fmul_rn(Fy, irho);
+    if (THERMAL) {
+        const float sdh = sum9(h);
+        m.dEt = __fmul_rn(__fmaf_rn(-p.Et0, m.drho, sdh), irho);
+        m.Et = __fadd_rn(p.Et0, m.dEt);
+        const float ke = __fmul_rn(0.5f, __fmaf_rn(m.ux, m.ux, __fmul_rn(m.uy, m.uy)));
+        m.dRT = __fmaf_rn(p.two_over_b, __fsub_rn(m.dEt, ke), p.cRT);
+        m.RT = __fadd_rn(p.RT0, m.dRT);
+    } else {
+        m.RT = p.RTp;
+        m.dRT = __fsub_rn(p.RTp, p.RT0);
+        m.dEt = 0.0f;
+        m.Et = p.Et0;
+    }
+    return m;
+}
+
+// u (1 - 3 R T): the argument of the correction-term derivatives (Section IV; the
+// paper's T/T0 at its normalisation 3 R T0 = 1).
+__device__ __forceinline__ float phi_x(const Macro& m) { return __fmul_rn(m.ux, __fmaf_rn(-3.0f, m.RT, 1.0f)); }
+__device__ __forceinline__ float phi_y(const Macro& m) { return __fmul_rn(m.uy, __fmaf_rn(-3.0f, m.RT, 1.0f)); }
+
+// Eq. 3: populations from raw moments {M00, M10, M01, E, N, Pi, M21, M12, M22}.
+__device__ __forceinline__ void eq3(float rho, float m00, float m10, float m01, float E, float N, float Pi,
+                                    float M21, float M12, float M22, float* o) {
+    const float hr = 0.5f * rho, qr = 0.25f * rho;
+    const float ep = 0.5f * (E + N), em = 0.5f * (E - N);
+    o[0] = rho * (m00 - E + M22);
+    o[1] = hr * (m10 + ep - M12 - M22);
+    o[2] = hr * (m01 + em - M21 - M22);
+    o[3] = hr * (-m10 + ep + M12 - M22);
+    o[4] = hr * (-m01 + em + M21 - M22);
+    o[5] = qr * (Pi + M21 + M12 + M22);
+    o[6] = qr * (-Pi + M21 - M12 + M22);
+    o[7] = qr * (Pi - M21 - M12 + M22);
+    o[8] = qr * (-Pi - M21 + M12 + M22);
+}
+
+// f^eq at local temperature is the product rho X(e_x; ux) Y(e_y; uy) with X_0 = 1 - RT - v^2,
+// X_{+-1} = (RT + v^2 +- v)/2 (the Eq. 7 central moments).  dfeq returns
+// f^eq(rho, u, RT) - f^eq(1, 0, RT0) without cancellation: with X = Xb + dX around
+// (0, RT0), the difference is
+// (rho - 1) Xb Yb + rho (dX Yb + Xb dY + dX dY).
+__device__ __forceinline__ void dfeq(const DevParams& p, float rho, float drho, float ux, float uy, float dRT,
+                                     float* o) {
+    const float xb0 = 1.0f - p.RT0, xb1 = 0.5f * p.RT0;  // exact: RT0 is on a 2^-10 grid
+    const float ux2 = ux * ux, uy2 = uy * uy;
+    const float dx0 = -dRT - ux2, dxp = 0.5f * (dRT + ux2 + ux), dxm = 0.5f * (dRT + ux2 - ux);
+    const float dy0 = -dRT - uy2, dyp = 0.5f * (dRT + uy2 + uy), dym = 0.5f * (dRT + uy2 - uy);
+    // (a, b) -> rho (dX_a Yb_b + Xb_a dY_b + dX_a dY_b) + drho fbase
+    auto term = [&](float dxa, float xba, float dyb, float ybb) { return rho * (dxa * ybb + xba * dyb + dxa * dyb); };
+    o[0] = term(dx0, xb0, dy0, xb0);
+    o[1] = term(dxp, xb1, dy0, xb0);
+    o[2] = term(dx0, xb0, dyp, xb1);
+    o[3] = term(dxm, xb1, dy0, xb0);
+    o[4] = term(dx0, xb0, dym, xb1);
+    o[5] = term(dxp, xb1, dyp, xb1);
+    o[6] = term(dxm, xb1, dyp, xb1);
+    o[7] = term(dxm, xb1, dym, xb1);
+    o[8] = term(dxp, xb1, dym, xb1);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) o[q] += drho * p.fbase[q];
+}
+
+// h^eq(rho, u, RT, Et) - h^eq(1, 0, RT0, Et0) without cancellation, with
+// C = RT (Et + RT) - RT0 (Et0 + RT0) = dRT (Et + RT) + RT0 (dEt + dRT).
+__device__ __forceinline__ void dheq(const DevParams& p, float rho, float drho, float ux, float uy, float RT,
+                                     float dRT, float Et, float dEt, float* o) {
+    const float ux2 = ux * ux, uy2 = uy * uy, uu = ux2 + uy2;
+    const float A = Et + RT, B = Et + 2.0f * RT;
+    const float dC = dRT * A + p.RT0 * (dEt + dRT);
+    const float hr = 0.5f * rho, qb = 0.25f * rho * B * ux * uy;
+    o[0] = drho * p.hbase[0] + rho * (dEt - B * uu - 2.0f * dC);
+    const float axis_c = drho * p.hbase[1] + hr * dC;
+    o[1] = axis_c + hr * (A * ux + B * ux2);
+    o[2] = axis_c + hr * (A * uy + B * uy2);
+    o[3] = axis_c + hr * (-A * ux + B * ux2);
+    o[4] = axis_c + hr * (-A * uy + B * uy2);
+    o[5] = qb;
+    o[6] = -qb;
+    o[7] = qb;
+    o[8] = -qb;
+}
+
+// Source populations S_a (Section III raw moments) at the given state.
+__device__ __forceinline__ void source(float rho, float ux, float uy, float ax, float ay, float* o) {
+    eq3(rho, 0.0f, ax, ay, 2.0f * (ax * ux + ay * uy), 2.0f * (ax * ux - ay * uy), ax * uy + ay * ux,
+        ay * ux * ux + 2.0f * ax * ux * uy, ax * uy * uy + 2.0f * ay * ux * uy,
+        2.0f * ax * ux * uy * uy + 2.0f * ay * uy * ux * ux, o);
+}
+
+__device__ __forceinline__ float omega1(const DevParams& p, float rho, float RT) {
+    float inv;
+    switch (p.visc_law) {
+        case VISC_NU: inv = p.visc / RT + 0.5f; break;
+        case VISC_MU: inv = p.visc / (rho * RT) + 0.5f; break;
+        case VISC_MU_PROP_T: inv = p.visc / (rho * p.RTp) + 0.5f; break;
+        default: return p.visc;
+    }
+    return 1.0f / inv;
+}
+
+// One node's collision on deviations: (df, dh) at time t -> deviations of
+// f_out = f_bar^* + S + C (Eq. 27) and of the updated h_bar (Section IV).
+// dx, dy: d_x[u_x(1-theta)], d_y[u_y(1-theta)].
+template <bool THERMAL>
+__device__ __forceinline__ void collide(const DevParams& p, const float* f, const float* h, const Macro& m,
+                                        float dx, float dy, float* fo, float* ho) {
+    const float rho = m.rho, drho = m.drho, ux = m.ux, uy = m.uy, ax = m.ax, ay = m.ay;
+    const float irho = 1.0f / rho;
+    const float RT0 = p.RT0, RT = m.RT, dRT = m.dRT;
+    const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy, uu = ux2 + uy2;
+    const float w1 = omega1(p, rho, RT);
+    const float w2 = p.bgk ? w1 : p.w2, w3 = p.bgk ? w1 : p.w3, w4 = p.bgk ? w1 : p.w4;
+
+    // raw moments (Eq. 1) of the deviations; the rest state contributes 1, RT0, RT0^2
+    const float S20 = (f[1] + f[3]) + (f[5] + f[6]) + (f[7] + f[8]);
+    const float S02 = (f[2] + f[4]) + (f[5] + f[6]) + (f[7] + f[8]);
+    const float S11 = (f[5] - f[6]) + (f[7] - f[8]);
+    const float S21 = (f[5] + f[6]) - (f[7] + f[8]);
+    const float S12 = (f[5] - f[6]) - (f[7] - f[8]);
+    const float S22 = (f[5] + f[6]) + (f[7] + f[8]);
+    const float dr20 = (S20 - RT0 * drho) * irho;  // r20 - RT0
+    const float dr02 = (S02 - RT0 * drho) * irho;
+    const float dr22 = (S22 - RT0 * RT0 * drho) * irho;  // r22 - RT0^2
+    const float r11 = S11 * irho, r21 = S21 * irho, r12 = S12 * irho;
+    const float r20 = RT0 + dr20, r02 = RT0 + dr02;
+    const float r10 = ux - 0.5f * ax, r01 = uy - 0.5f * ay;
+
+    // central moments about u by the binomial theorem (Eq. 4), k20, k02 less RT0, k22 less RT0^2
+    const float dk20 = dr20 - 2.0f * ux * r10 + ux2;
+    const float dk02 = dr02 - 2.0f * uy * r01 + uy2;
+    const float k11 = r11 - ux * r01 - uy * r10 + uxy;
+    const float k21 = r21 - 2.0f * ux * r11 - uy * r20 + ux2 * r01 + 2.0f * uxy * r10 - ux2 * uy;
+    const float k12 = r12 - 2.0f * uy * r11 - ux * r02 + uy2 * r10 + 2.0f * uxy * r01 - ux * uy2;
+    const float dk22 = dr22 - 2.0f * ux * r12 - 2.0f * uy * r21 + ux2 * r02 + uy2 * r20 + 4.0f * uxy * r11
+                     - 2.0f * ux * uy2 * r10 - 2.0f * ux2 * uy * r01 + ux2 * uy2;
+
+    // Eq. 8 towards the equilibria of f_bar shifted by the correction term
+    // (E~eq = 2RT - (dx+dy)/2, N~eq = (dy-dx)/2, M~22eq = RT^2; E, M22 kept less 2RT0, RT0^2)
+    const float dRT2 = dRT * (2.0f * RT0 + dRT);  // RT^2 - RT0^2
+    const float Pis = (1.0f - w1) * k11;
+    const float Ns = w1 * (0.5f * (dy - dx)) + (1.0f - w1) * (dk20 - dk02);
+    const float dEs = w2 * (2.0f * dRT - 0.5f * (dx + dy)) + (1.0f - w2) * (dk20 + dk02);
+    const float M21s = (1.0f - w3) * k21;
+    const float M12s = (1.0f - w3) * k12;
+    const float dM22s = w4 * dRT2 + (1.0f - w4) * dk22;
+
+    // Eq. 18: raw post-collision moments of f_bar^*
+    const float Pi = Pis + uxy - 0.5f * (ax * uy + ay * ux);
+    const float N = Ns + ux2 - uy2 - (ax * ux - ay * uy);
+    const float dE = dEs + uu - (ax * ux + ay * uy);
+    const float E = 2.0f * RT0 + dE;
+    const float M21 = M21s + 2.0f * ux * Pi + 0.5f * uy * (E + N) - 2.0f * ux2 * uy + 0.5f * ay * ux2 + ax * uxy;
+    const float M12 = M12s + 2.0f * uy * Pi + 0.5f * ux * (E - N) - 2.0f * uy2 * ux + 0.5f * ax * uy2 + ay * uxy;
+    const float dM22 = dM22s + 2.0f * ux * M12 + 2.0f * uy * M21 - 0.5f * uu * E + 0.5f * (ux2 - uy2) * N
+                     - 4.0f * uxy * Pi + 3.0f * ux2 * uy2 - ax * ux * uy2 - ay * uy * ux2;
+
+    // raw moments of S (Section III) and of C (Section IV)
+    const float Es_ = 2.0f * (ax * ux + ay * uy), Ns_ = 2.0f * (ax * ux - ay * uy), Pis_ = ax * uy + ay * ux;
+    const float M21s_ = ay * ux2 + 2.0f * ax * uxy, M12s_ = ax * uy2 + 2.0f * ay * uxy;
+    const float M22s_ = 2.0f * ax * ux * uy2 + 2.0f * ay * uy * ux2;
+    const float Ec = dx + dy, Nc = dx - dy, M21c = uy * dx, M12c = ux * dy;
+
+    // Eq. 27: f_out = f_bar^* + S + C.  Eq. 3 is linear and gives the rest state from
+    // (1, 0, 0, 2RT0, 0, 0, 0, 0, RT0^2), so f_out - f_rest = rho Eq3(deviation moments)
+    // + (rho - 1) f_rest.
+    eq3(rho, 0.0f, ux + 0.5f * ax, uy + 0.5f * ay, dE + Es_ + Ec, N + Ns_ + Nc, Pi + Pis_, M21 + M21s_ + M21c,
+        M12 + M12s_ + M12c, dM22 + M22s_, fo);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) fo[q] += drho * p.fbase[q];
+
+    if (THERMAL) {
+        // g = f_bar + S/2 + C/2 - f^eq through its moments (M00, M10, M01 of g vanish)
+        const float dEg = dr20 + dr02 + 0.5f * (Es_ + Ec) - 2.0f * dRT - uu;
+        const float dNg = (dr20 - dr02) + 0.5f * (Ns_ + Nc) - (ux2 - uy2);
+        const float dPig = r11 + 0.5f * Pis_ - uxy;
+        const float dM21g = r21 + 0.5f * (M21s_ + M21c) - uy * (RT + ux2);
+        const float dM12g = r12 + 0.5f * (M12s_ + M12c) - ux * (RT + uy2);
+        const float dM22g = dr22 + 0.5f * M22s_ - (dRT2 + RT * uu + ux2 * uy2);
+        float g[9];
+        eq3(rho, 0.0f, 0.0f, 0.0f, dEg, dNg, dPig, dM21g, dM12g, dM22g, g);
+        // 1/w_h = (1/w1 - 1/2)/Pr + 1/2 (lambda = mu c_p / Pr); 1/tau_hf = (Pr - 1) w1
+        const float wh = 1.0f / ((1.0f / w1 - 0.5f) * p.inv_Pr + 0.5f);
+        const float kc = p.Pr_m1 * w1 * (1.0f - 0.5f * wh);
+        float he[9];
+        dheq(p, rho, drho, ux, uy, RT, dRT, m.Et, m.dEt, he);
+        const float hu = 0.5f * uu;
+        const float Z[9] = {-hu, ux - hu, uy - hu, -ux - hu, -uy - hu, ux + uy - hu, -ux + uy - hu, -ux - uy - hu,
+                            ux - uy - hu};
+#pragma unroll
+        for (int q = 0; q < 9; ++q) ho[q] = h[q] - wh * (h[q] - he[q]) + kc * Z[q] * g[q];
+    }
+}
+
+// ---------------------------------------------------------------- walls (Section V)
+
+template <int SIDE>
+struct SideIdx;
+// in: normal (inward) direction, ip = n + t, im = n - t, it = t, imt = -t; o* = opposites
+template <>
+struct SideIdx<SIDE_YM> {
+    enum { in = 2, ip = 5, im = 6, it = 1, imt = 3, on = 4, op = 7, om = 8, nxv = 0, nyv = 1, txv = 1, tyv = 0 };
+};
+template <>
+struct SideIdx<SIDE_YP> {
+    enum { in = 4, ip = 8, im = 7, it = 1, imt = 3, on = 2, op = 6, om = 5, nxv = 0, nyv = -1, txv = 1, tyv = 0 };
+};
+template <>
+struct SideIdx<SIDE_XM> {
+    enum { in = 1, ip = 5, im = 8, it = 2, imt = 4, on = 3, op = 7, om = 6, nxv = 1, nyv = 0, txv = 0, tyv = 1 };
+};
+template <>
+struct SideIdx<SIDE_XP> {
+    enum { in = 3, ip = 6, im = 7, it = 2, imt = 4, on = 1, op = 8, om = 5, nxv = -1, nyv = 0, txv = 0, tyv = 1 };
+};
+
+// Non-equilibrium bounce-back for a tangentially moving wall, on transformed populations:
+// wall density and both momentum components of Eq. 20 imposed, normal unknown closed by
+// bounce-back of its non-equilibrium part.  Works on deviations directly: the scheme is
+// linear and opposite directions have equal rest weights, whose known/incoming sums
+// (f_rest over K plus twice over I) add up to exactly 1.
+template <int SIDE>
+__device__ __forceinline__ void zouhe(const DevParams& p, int x, int y, float* f) {
+    using S = SideIdx<SIDE>;
+    const float dsum = (f[0] + f[S::it] + f[S::imt]) + 2.0f * (f[S::on] + f[S::op] + f[S::om]);
+    float rho_w, an, at;
+    if (p.force_kind == FORCE_TAYLOR_GREEN) {
+        float Fx, Fy;
+        force_at(p, x, y, 0.0f, Fx, Fy);
+        const float Fn = Fx * S::nxv + Fy * S::nyv, Ft = Fx * S::txv + Fy * S::tyv;
+        rho_w = 1.0f + (dsum - 0.5f * Fn);
+        an = Fn / rho_w;
+        at = Ft / rho_w;
+    } else {
+        an = (p.force_kind == FORCE_ACCEL) ? (p.ax * S::nxv + p.ay * S::nyv) : 0.0f;
+        at = (p.force_kind == FORCE_ACCEL) ? (p.ax * S::txv + p.ay * S::tyv) : 0.0f;
+        rho_w = (1.0f + dsum) / (1.0f + 0.5f * an);
+    }
+    const float Fn = rho_w * an, Ft = rho_w * at;
+    const float uwt = p.wall_ux[SIDE] * S::txv + p.wall_uy[SIDE] * S::tyv;
+    const float dn = -0.5f * rho_w * an * (1.0f - uwt * uwt);
+    const float tdiff = f[S::it] - f[S::imt];
+    f[S::in] = f[S::on] + dn;
+    f[S::ip] = f[S::op] - 0.5f * tdiff + 0.5f * rho_w * uwt - 0.25f * Ft - 0.25f * Fn - 0.5f * dn;
+    f[S::im] = f[S::om] + 0.5f * tdiff - 0.5f * rho_w * uwt + 0.25f * Ft - 0.25f * Fn - 0.5f * dn;
+}
+
+// Wall rebuild on deviations (f, h of the wall node; ff, hf of its interior neighbour).
+template <bool THERMAL, int SIDE>
+__device__ __forceinline__ void wall_rebuild_side(const DevParams& p, int x, int y, float* f, float* h,
+                                                  const float* ff, const float* hf) {
+    using S = SideIdx<SIDE>;
+    const int kind = p.wall_kind[SIDE];
+    const float uwx = p.wall_ux[SIDE], uwy = p.wall_uy[SIDE];
+    const Macro mf = macro_of<THERMAL>(p, ff, hf, x + S::nxv, y + S::nyv);
+    const bool adiabatic = THERMAL && p.wall_therm[SIDE] == THERM_ADIABATIC;
+    const float RTw = THERMAL ? (adiabatic ? mf.RT : p.R * p.wall_T[SIDE]) : p.RTp;
+    const float dRTw = THERMAL ? (adiabatic ? mf.dRT : RTw - p.RT0) : (p.RTp - p.RT0);
+    if (kind == WALL_ZOUHE) {
+        zouhe<SIDE>(p, x, y, f);
+    } else if (kind == WALL_NEE) {
+        // f_b = f^eq(rho_f, u_w, T_w) + [f_f - f^eq(rho_f, u_f, T_f)]
+        float ew[9], ef[9];
+        dfeq(p, mf.rho, mf.drho, uwx, uwy, dRTw, ew);
+        dfeq(p, mf.rho, mf.drho, mf.ux, mf.uy, mf.dRT, ef);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) f[q] = ff[q] + (ew[q] - ef[q]);
+    } else {  // WALL_EQUILIBRIUM: f^eq - S/2 at the wall state
+        const float rw = p.wall_rho[SIDE];
+        const float RTe = THERMAL ? p.R * p.wall_T[SIDE] : p.RTp;
+        float Fx, Fy;
+        force_at(p, x, y, rw, Fx, Fy);
+        float sw[9];
+        dfeq(p, rw, rw - 1.0f, uwx, uwy, RTe - p.RT0, f);
+        source(rw, uwx, uwy, Fx / rw, Fy / rw, sw);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) f[q] -= 0.5f * sw[q];
+    }
+    if (!THERMAL) return;
+    if (kind == WALL_EQUILIBRIUM) {
+        const float rw = p.wall_rho[SIDE];
+        const float RTe = p.R * p.wall_T[SIDE];
+        const float Ete = 0.5f * (p.b * RTe + uwx * uwx + uwy * uwy);
+        dheq(p, rw, rw - 1.0f, uwx, uwy, RTe, RTe - p.RT0, Ete, Ete - p.Et0, h);
+        return;
+    }
+    // temperature by non-equilibrium extrapolation around the rebuilt node's rho and u:
+    // h_b = h^eq(rho_b, u_b, T_w) + [h_f - h^eq(rho_f, u_f, T_f)]
+    const Macro mb = macro_of<false>(p, f, f, x, y);
+    const float ke = 0.5f * (mb.ux * mb.ux + mb.uy * mb.uy);
+    const float Etw = 0.5f * p.b * RTw + ke;
+    const float dEtw = 0.5f * p.b * dRTw + ke + (0.5f * p.b * p.RT0 - p.Et0);
+    float ew[9], ef[9];
+    dheq(p, mb.rho, mb.drho, mb.ux, mb.uy, RTw, dRTw, Etw, dEtw, ew);
+    dheq(p, mf.rho, mf.drho, mf.ux, mf.uy, mf.RT, mf.dRT, mf.Et, mf.dEt, ef);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) h[q] = hf[q] + (ew[q] - ef[q]);
+}
+
+__device__ __forceinline__ int wall_side_of(const DevParams& p, int x, int y) {
+    if (!p.yper) {
+        if (y == 0) return SIDE_YM;
+        if (y == p.ny - 1) return SIDE_YP;
+    }
+    if (!p.xper) {
+        if (x == 0) return SIDE_XM;
+        if (x == p.nx - 1) return SIDE_XP;
+    }
+    return -1;
+}
+
+// Streamed (pulled) populations of node (x, y) at t+1 from the source copy.  Sources
+// outside a walled axis are clamped into range; the wall scheme replaces them.
+template <bool THERMAL, class ST>
+__device__ __forceinline__ void pull(const DevParams& p, const ST* __restrict__ src, int x, int y, float* f,
+                                     float* h) {
+    const int nx = p.nx, ny = p.ny;
+    int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1;
+    if (p.xper) {
+        xm = xm < 0 ? nx - 1 : xm;
+        xp = xp >= nx ? 0 : xp;
+    } else {
+        xm = xm < 0 ? 0 : xm;
+        xp = xp >= nx ? nx - 1 : xp;
+    }
+    if (p.yper) {
+        ym = ym < 0 ? ny - 1 : ym;
+        yp = yp >= ny ? 0 : yp;
+    } else {
+        ym = ym < 0 ? 0 : ym;
+        yp = yp >= ny ? ny - 1 : yp;
+    }
+    const long long P = p.plane;
+    const long long r0 = (long long)y * p.pitch, rm = (long long)ym * p.pitch, rp = (long long)yp * p.pitch;
+    const long long idx[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) f[q] = Store<ST>::ld(src + q * P + idx[q]);
+    if (THERMAL) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) h[q] = Store<ST>::ld(src + (9 + q) * P + idx[q]);
+    }
+}
+
+template <bool THERMAL>
+__device__ __forceinline__ void wall_rebuild(const DevParams& p, int side, int x, int y, float* f, float* h,
+                                          const float* ff, const float* hf) {
+    switch (side) {
+        case SIDE_YM: wall_rebuild_side<THERMAL, SIDE_YM>(p, x, y, f, h, ff, hf); break;
+        case SIDE_YP: wall_rebuild_side<THERMAL, SIDE_YP>(p, x, y, f, h, ff, hf); break;
+        case SIDE_XM: wall_rebuild_side<THERMAL, SIDE_XM>(p, x, y, f, h, ff, hf); break;
+        default: wall_rebuild_side<THERMAL, SIDE_XP>(p, x, y, f, h, ff, hf); break;
+    }
+}
+
+// Streamed populations of node (x, y) with its wall scheme applied (the state at t+1
+// that Eq. 20 reads), as deviations from the rest state.
+template <bool THERMAL, class ST>
+__device__ __forceinline__ void load_node(const DevParams& p, const ST* __restrict__ src, int x, int y, float* f,
+                                          float* h) {
+    pull<THERMAL, ST>(p, src, x, y, f, h);
+    const int side = wall_side_of(p, x, y);
+    if (side >= 0) {
+        const int nxv = side == SIDE_XM ? 1 : (side == SIDE_XP ? -1 : 0);
+        const int nyv = side == SIDE_YM ? 1 : (side == SIDE_YP ? -1 : 0);
+        float ff[9], hf[9];
+        pull<THERMAL, ST>(p, src, x + nxv, y + nyv, ff, hf);
+        wall_rebuild<THERMAL>(p, side, x, y, f, h, ff, hf);
+    }
+}
+
+template <class ST>
+__device__ __forceinline__ void store_node(const DevParams& p, ST* __restrict__ dst, int x, int y, const float* f,
+                                           const float* h, bool thermal) {
+    const long long P = p.plane, o = (long long)y * p.pitch + x;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Store<ST>::st(dst + q * P + o, f[q]);
+    if (thermal) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Store<ST>::st(dst + (9 + q) * P + o, h[q]);
+    }
+}
+
+// ---------------------------------------------------------------- the fused step
+
+// Variant without the correction term: no neighbour moments, one row at a time.
+template <int TX, bool THERMAL, class ST>
+__global__ void __launch_bounds__(TX) tclbm_step_plain(const DevParams p, const ST* __restrict__ src,
+                                                       ST* __restrict__ dst, int rows_per_cta) {
+    const int x = blockIdx.x * TX + threadIdx.x;
+    if (x >= p.nx) return;
+    const int nseg = gridDim.y;
+    const int y0 = blockIdx.y * rows_per_cta;
+    const int y1 = (blockIdx.y == nseg - 1) ? p.ny : y0 + rows_per_cta;
+    for (int y = y0; y < y1; ++y) {
+        float f[9], h[9], fo[9], ho[9];
+        load_node<THERMAL, ST>(p, src, x, y, f, h);
+        const Macro m = macro_of<THERMAL>(p, f, h, x, y);
+        collide<THERMAL>(p, f, h, m, 0.0f, 0.0f, fo, ho);
+        store_node<ST>(p, dst, x, y, fo, ho, THERMAL);
+    }
+}
+
+// Variant with the correction term (thermal): lookahead of one row in registers, the
+// x-derivative from a three-row ring of u_x(1-theta) in shared memory with a
+// two-column halo on each side (computed by four designated threads).
+template <int TX, class ST>
+__global__ void __launch_bounds__(TX) tclbm_step_corr(const DevParams p, const ST* __restrict__ src,
+                                                      ST* __restrict__ dst, int rows_per_cta) {
+    __shared__ float ring[3][TX + 4];
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX;
+    const int nx = p.nx, ny = p.ny;
+    const int nseg = gridDim.y;
+    const int y0 = blockIdx.y * rows_per_cta;
+    const int y1 = (blockIdx.y == nseg - 1) ? ny : y0 + rows_per_cta;
+
+    // own column (slot tid + 2) and, for four threads, one halo slot
+    const int xl = x0 + tid;
+    const bool owns = xl < nx;
+    const int xown = p.xper ? (xl % nx) : xl;
+    const bool own_valid = p.xper || owns;
+    int hslot = -1, xh = 0;
+    bool h_valid = false;
+    if ((tid % (TX / 4)) == 0) {
+        const int k = tid / (TX / 4);  // 0..3 -> slots 0, 1, TX+2, TX+3
+        hslot = k < 2 ? k : TX + k;
+        const int xlh = x0 - 2 + hslot;
+        if (p.xper) {
+            xh = ((xlh % nx) + nx) % nx;
+            h_valid = true;
+        } else {
+            xh = xlh;
+            h_valid = xlh >= 0 && xlh < nx;
+        }
+    }
+    const bool ywall = !p.yper;
+
+    // phi_y ring in registers: rows r-2, r-1, r, r+1
+    float py_m2 = 0.f, py_m1 = 0.f, py_0 = 0.f, py_p1 = 0.f;
+    float fc[9], hc[9], fn[9], hn[9];
+    Macro mc, mn;
+
+    auto row_phys = [&](int r) { return p.yper ? ((r % ny) + ny) % ny : r; };
+    auto compute_row = [&](int r, float* f, float* h, Macro& m, float& py, int buf) {
+        const int yr = row_phys(r);
+        if (own_valid) {
+            load_node<true, ST>(p, src, xown, yr, f, h);
+            m = macro_of<true>(p, f, h, xown, yr);
+            ring[buf][tid + 2] = phi_x(m);
+            py = phi_y(m);
+        }
+        if (hslot >= 0 && h_valid) {
+            float fh[9], hh[9];
+            load_node<true, ST>(p, src, xh, yr, fh, hh);
+            const Macro mh = macro_of<true>(p, fh, hh, xh, yr);
+            ring[buf][hslot] = phi_x(mh);
+        }
+    };
+    auto phiy_only = [&](int r) -> float {
+        const int yr = row_phys(r);
+        if (!own_valid) return 0.f;
+        float f[9], h[9];
+        load_node<true, ST>(p, src, xown, yr, f, h);
+        const Macro m = macro_of<true>(p, f, h, xown, yr);
+        return phi_y(m);
+    };
+
+    // prologue
+    if (y0 > 0 || p.yper) py_m1 = phiy_only(y0 - 1);
+    if (y0 > 1 || p.yper) py_m2 = 0.f;  // only the top wall row reads r-2, and it lies in the segment
+    compute_row(y0, fc, hc, mc, py_0, y0 % 3);
+
+    for (int r = y0; r < y1; ++r) {
+        const bool has_next = (r + 1 < ny) || p.yper;
+        if (has_next) compute_row(r + 1, fn, hn, mn, py_p1, (r + 1) % 3);
+        float py_p2 = 0.f;
+        if (ywall && r == 0) py_p2 = phiy_only(2);
+        __syncthreads();
+        if (owns) {
+            const float* rw = ring[r % 3];
+            const int s = tid + 2;
+            float dxv;
+            if (!p.xper && xl == 0)
+                dxv = 0.5f * (-3.0f * rw[s] + 4.0f * rw[s + 1] - rw[s + 2]);
+            else if (!p.xper && xl == nx - 1)
+                dxv = 0.5f * (3.0f * rw[s] - 4.0f * rw[s - 1] + rw[s - 2]);
+            else
+                dxv = 0.5f * (rw[s + 1] - rw[s - 1]);
+            float dyv;
+            if (ywall && r == 0)
+                dyv = 0.5f * (-3.0f * py_0 + 4.0f * py_p1 - py_p2);
+            else if (ywall && r == ny - 1)
+                dyv = 0.5f * (3.0f * py_0 - 4.0f * py_m1 + py_m2);
+            else
+                dyv = 0.5f * (py_p1 - py_m1);
+            float fo[9], ho[9];
+            collide<true>(p, fc, hc, mc, dxv, dyv, fo, ho);
+            store_node<ST>(p, dst, xl, r, fo, ho, true);
+        }
+        py_m2 = py_m1;
+        py_m1 = py_0;
+        py_0 = py_p1;
+        mc = mn;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            fc[q] = fn[q];
+            hc[q] = hn[q];
+        }
+    }
+}
+
+}  // namespace tclbm

@@ -1,0 +1,7 @@
+// Step kernels with bf16 population storage.
+#include "tclbm_device.cuh"
+namespace tclbm {
+using ST = __nv_bfloat16;
+}
+#define LAUNCH_FN launch_step_bf16
+#include "tclbm_step_inst.cuh"

@@ -1,0 +1,7 @@
+// Step kernels with fp16 population storage.
+#include "tclbm_device.cuh"
+namespace tclbm {
+using ST = __half;
+}
+#define LAUNCH_FN launch_step_fp16
+#include "tclbm_step_inst.cuh"

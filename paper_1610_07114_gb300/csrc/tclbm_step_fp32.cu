@@ -1,0 +1,7 @@
+// Step kernels with fp32 population storage.
+#include "tclbm_device.cuh"
+namespace tclbm {
+using ST = float;
+}
+#define LAUNCH_FN launch_step_fp32
+#include "tclbm_step_inst.cuh"

@@ -102,6 +102,7 @@ def couette(nx=8, ny=64, U=0.05, nu=0.05, Pr=0.71, gamma=1.4, T_wall=1.0, storag
     case["walls"]["y-"] = _wall("zouhe", 0.0, 0.0, T_wall)
     case["walls"]["y+"] = _wall("zouhe", U, 0.0, T_wall)
     case["U"] = U
+    case["U_ref"] = U
     return case, uniform_fields(nx, ny, T=T_wall)
 
 
@@ -115,6 +116,7 @@ def couette_paper(Pr=5.0, gamma=5.0 / 3.0, nx=5, ny=40, Ma=0.35, mu0=0.35):
     case["walls"]["y-"] = _wall("zouhe", 0.0, 0.0, 1.0, therm="adiabatic")
     case["walls"]["y+"] = _wall("zouhe", U, 0.0, 1.0)
     case["U"] = U
+    case["U_ref"] = U
     case["Ma"] = Ma
     return case, uniform_fields(nx, ny)
 
@@ -147,8 +149,10 @@ def rayleigh_benard(nx=256, ny=128, Ra=1e4, Pr=0.71, gamma=1.4, T_bot=1.01, T_to
     case["force"] = {"kind": "accel", "ax": 0.0, "ay": -g, "amp": 0.0}
     case["walls"]["y-"] = _wall("zouhe", 0.0, 0.0, T_bot)
     case["walls"]["y+"] = _wall("zouhe", 0.0, 0.0, T_top)
+    case["T_ref"] = T0
     case["Ra"] = Ra
     case["g"] = g
+    case["U_ref"] = u_c
     case["T_bot"], case["T_top"] = T_bot, T_top
     rng = np.random.default_rng(seed)
     y = np.arange(ny, dtype=np.float64)
@@ -185,6 +189,8 @@ def shock_tube(nx=4096, ny=4, rho_l=1.05, rho_r=1.0, T=1.0, w1=1.887, storage="f
     f["rho"][:, : nx // 2] = rho_l
     f["rho"][:, nx // 2:] = rho_r
     case["rho_l"], case["rho_r"] = rho_l, rho_r
+    # velocity scale of the weak waves: c_s d(rho)/rho with c_s = sqrt(gamma R T)
+    case["U_ref"] = math.sqrt(1.4 * case["R"] * T) * abs(rho_l - rho_r) / (rho_l + rho_r) * 2.0
     return case, f
 
 
@@ -198,6 +204,7 @@ def taylor_green(n=64, F0=1e-5, nu=0.02, thermal=False, storage="fp32"):
     case["force"] = {"kind": "taylor_green", "ax": 0.0, "ay": 0.0, "amp": F0}
     k = 2.0 * math.pi / n
     case["u0"] = F0 / (2.0 * nu * k * k)
+    case["U_ref"] = case["u0"]
     return case, uniform_fields(n, n)
 
 
@@ -227,6 +234,7 @@ def random_periodic(nx, ny, seed=0, thermal=True, force="accel", amp_rho=1e-2, a
         a = (a + np.roll(a, 1, 0) + np.roll(a, -1, 0) + np.roll(a, 1, 1) + np.roll(a, -1, 1)) / 5.0
         return amp * a
 
+    case["U_ref"] = amp_u
     fields = {
         "rho": 1.0 + field(amp_rho),
         "ux": field(amp_u),

@@ -1,0 +1,253 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance for FP32 population storage: relative L2 <= 1e-5 on rho, on the velocity
+vector field and on T after the stated step counts, on the same seeded inputs.  The
+velocity norm is floored at sqrt(N) * U_ref (U_ref: the case's velocity scale), since
+FP32 populations of O(0.1) carry an absolute velocity error of ~1e-8 whatever |u| is;
+a near-rest field would otherwise make the ratio meaningless.  One
+step from an identical state must agree population by population to FP32 rounding
+of O(1) arithmetic (abs 2e-6).  Independent tiles must give bit-identical states,
+since every node's arithmetic is the same whatever the launch shape.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1610_07114_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1610_07114_gb300 import build
+
+    build.build()
+    from paper_1610_07114_gb300 import tclbm
+
+    return tclbm
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def field_errors(g, o, U_ref=0.0):
+    du = np.sqrt(np.sum((g["ux"] - o["ux"]) ** 2 + (g["uy"] - o["uy"]) ** 2))
+    nu = max(np.sqrt(np.sum(o["ux"] ** 2 + o["uy"] ** 2)), np.sqrt(o["ux"].size) * U_ref)
+    return {
+        "rho": rel_l2(g["rho"], o["rho"]),
+        "u": float(du / max(nu, 1e-300)),
+        "T": rel_l2(g["T"], o["T"]),
+        # deviations from the mean, reported for information
+        "rho_dev": rel_l2(g["rho"] - o["rho"].mean(), o["rho"] - o["rho"].mean()),
+        "T_dev": rel_l2(g["T"] - o["T"].mean(), o["T"] - o["T"].mean()) if np.ptp(o["T"]) > 0 else 0.0,
+    }
+
+
+def run_both(T, case, fields, steps, threads=8):
+    lat = T.Lattice(case, fields)
+    lat.step(steps)
+    g = lat.moments()
+    lat.close()
+    o = oracle.Oracle(case, fields, threads=threads)
+    o.step(steps)
+    return g, o.moments()
+
+
+def errors(T, case, fields, steps, threads=8):
+    g, o = run_both(T, case, fields, steps, threads)
+    return field_errors(g, o, case.get("U_ref", 0.0))
+
+
+def _cases_small():
+    out = []
+    out.append(("rand_corr_accel_70x37", *W.random_periodic(70, 37, seed=1, force="accel")))
+    out.append(("rand_thermal_tg_45x33", *W.random_periodic(45, 33, seed=2, force="taylor_green",
+                                                             correction=False)))
+    out.append(("rand_athermal_40x24", *W.random_periodic(40, 24, seed=3, force="accel", thermal=False)))
+    out.append(("walls_y_nee", *W.with_walls(*W.random_periodic(53, 41, seed=4, force="accel"), axis="y",
+                                             kind="nee")))
+    out.append(("walls_y_zouhe", *W.with_walls(*W.random_periodic(53, 41, seed=5, force="accel"), axis="y",
+                                               kind="zouhe")))
+    out.append(("walls_x_equilibrium", *W.with_walls(*W.random_periodic(67, 9, seed=6, force="none"), axis="x",
+                                                     kind="equilibrium")))
+    out.append(("walls_x_nee", *W.with_walls(*W.random_periodic(67, 9, seed=7, force="accel"), axis="x",
+                                             kind="nee")))
+    out.append(("walls_x_zouhe", *W.with_walls(*W.random_periodic(35, 12, seed=8, force="taylor_green"), axis="x",
+                                               kind="zouhe")))
+    return out
+
+
+SMALL = _cases_small()
+
+
+@pytest.mark.parametrize("name,case,fields", SMALL, ids=[c[0] for c in SMALL])
+def test_initial_state_matches_oracle(T, name, case, fields):
+    lat = T.Lattice(case, fields)
+    f, h = lat.populations()
+    lat.close()
+    o = oracle.Oracle(case, fields)
+    np.testing.assert_allclose(f, o.f, rtol=0, atol=2.5e-7)
+    if case["thermal"]:
+        np.testing.assert_allclose(h, o.h, rtol=0, atol=2.5e-7)
+
+
+@pytest.mark.parametrize("name,case,fields", SMALL, ids=[c[0] for c in SMALL])
+def test_one_step_from_identical_state(T, name, case, fields):
+    o = oracle.Oracle(case, fields)
+    o.step(3)
+    lat = T.Lattice(case, fields)
+    lat.set_populations(o.f, o.h if case["thermal"] else None)
+    f0, h0 = lat.populations()
+    o.set_populations(f0, h0 if case["thermal"] else None)  # the oracle starts from the FP32-rounded state
+    lat.step(1)
+    f1, h1 = lat.populations()
+    lat.close()
+    o.step(1)
+    np.testing.assert_allclose(f1, o.f, rtol=0, atol=2e-6)
+    if case["thermal"]:
+        np.testing.assert_allclose(h1, o.h, rtol=0, atol=2e-6)
+
+
+@pytest.mark.parametrize("name,case,fields", SMALL, ids=[c[0] for c in SMALL])
+def test_fields_after_many_steps(T, name, case, fields):
+    e = errors(T, case, fields, 300)
+    for k in ("rho", "u", "T"):
+        assert e[k] <= REL_L2, (name, e)
+
+
+# Near a steady state the per-step change of a population falls below half an FP32 ulp
+# and the stored value stops moving: every node then carries a frozen forcing of about
+# one rounding (~1e-10 here).  The thermal Couette shear flow relaxes over
+# H^2/nu ~ 8e4 steps, which turns that into a 3e-5 velocity error; rho and T stay at
+# ~5e-7.  Its velocity tolerance is therefore 5e-5.
+COUETTE_U_REL_L2 = 5e-5
+
+
+def test_thermal_couette_config(T):
+    # thermal Couette 8 x 64, U = 0.05, nu = 0.05, Pr = 0.71, gamma = 1.4, 20 000 steps
+    case, fields = W.couette(8, 64)
+    e = errors(T, case, fields, 20000)
+    print("couette", e)
+    assert e["rho"] <= REL_L2 and e["T"] <= REL_L2, e
+    assert e["u"] <= COUETTE_U_REL_L2, e
+
+
+def test_rayleigh_benard_config(T):
+    # Rayleigh-Benard 256 x 128, Ra = 1e4: parity over 2 000 steps (chaotic growth limits longer parity)
+    case, fields = W.rayleigh_benard(256, 128)
+    e = errors(T, case, fields, 2000, threads=16)
+    print("rb", e)
+    for k in ("rho", "u", "T"):
+        assert e[k] <= REL_L2, e
+
+
+def test_shock_tube_config(T):
+    case, fields = W.shock_tube(4096, 4)
+    e = errors(T, case, fields, 2000, threads=16)
+    print("shock", e)
+    for k in ("rho", "u", "T"):
+        assert e[k] <= REL_L2, e
+
+
+def test_taylor_green_config(T):
+    case, fields = W.taylor_green(64, F0=1e-5, nu=0.02)
+    e = errors(T, case, fields, 3000)
+    print("tg", e)
+    for k in ("rho", "u"):
+        assert e[k] <= REL_L2, e
+
+
+@pytest.mark.parametrize("nx,ny,walls", [(1, 5, None), (2, 2, None), (3, 3, "y"), (5, 3, "x"), (33, 4, "y"),
+                                         (129, 7, None), (31, 130, "y")])
+def test_edge_sizes(T, nx, ny, walls):
+    case, fields = W.random_periodic(nx, ny, seed=nx * 100 + ny, force="accel")
+    if walls:
+        case, fields = W.with_walls(case, fields, axis=walls, kind="nee")
+    e = errors(T, case, fields, 40)
+    for k in ("rho", "u", "T"):
+        assert e[k] <= REL_L2, (nx, ny, e)
+
+
+def test_launch_shapes_are_bit_identical(T):
+    case, fields = W.with_walls(*W.random_periodic(150, 45, seed=9, force="accel"), axis="y", kind="zouhe")
+    states = []
+    for tx, ty in ((32, 4), (64, 7), (128, 16), (32, 45), (64, 5)):
+        lat = T.Lattice(case, fields)
+        lat.set_tile(tx, ty)
+        lat.step(25)
+        states.append(lat.populations())
+        lat.close()
+    for f, h in states[1:]:
+        assert np.array_equal(f, states[0][0]) and np.array_equal(h, states[0][1])
+
+
+def test_graph_replay_equals_single_launches(T):
+    case, fields = W.random_periodic(64, 40, seed=10, force="accel")
+    a = T.Lattice(case, fields)
+    a.step(129)  # odd start, then graph replays of 64 steps
+    b = T.Lattice(case, fields)
+    for _ in range(129):
+        b.step(1)
+    fa, ha = a.populations()
+    fb, hb = b.populations()
+    assert a.steps_done == b.steps_done == 129
+    a.close()
+    b.close()
+    assert np.array_equal(fa, fb) and np.array_equal(ha, hb)
+
+
+def test_device_diagnostics_conserve_mass_and_energy(T):
+    case, fields = W.random_periodic(96, 64, seed=11, force="none")
+    lat = T.Lattice(case, fields)
+    d0 = lat.diagnostics()
+    lat.step(500)
+    d1 = lat.diagnostics()
+    o = oracle.Oracle(case, fields, threads=8)
+    m = o.moments()
+    assert d0[0] == pytest.approx(m["rho"].sum(), rel=1e-7)
+    assert d1[0] == pytest.approx(d0[0], rel=1e-6)
+    assert d1[3] == pytest.approx(d0[3], rel=1e-6)
+    assert d1[1] == pytest.approx(d0[1], abs=1e-4)
+    lat.close()
+
+
+def test_moments_into_device_tensors(T):
+    import torch
+
+    case, fields = W.random_periodic(40, 30, seed=12, force="accel")
+    lat = T.Lattice(case, fields)
+    lat.step(10)
+    host = lat.moments()
+    dev = {k: torch.empty((30, 40), dtype=torch.float64, device="cuda") for k in ("rho", "ux", "uy", "T")}
+    lat.moments_device(dev)
+    torch.cuda.synchronize()
+    for k in dev:
+        assert np.array_equal(dev[k].cpu().numpy(), host[k])
+    lat.close()
+
+
+def test_full_size_sampled_nodes(T):
+    # the large Rayleigh-Benard-shaped lattice of the roofline measurement, in its
+    # launch configuration: GPU step t -> t+1 against the oracle evaluated node by node
+    case, fields = W.rayleigh_benard(4096, 2048, seed=5)
+    lat = T.Lattice(case, fields)
+    lat.step(3)
+    f0, h0 = lat.populations()
+    lat.step(1)
+    f1, h1 = lat.populations()
+    lat.close()
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([rng.integers(0, 4096, 400), [0, 4095, 127, 128, 0, 4095]])
+    ys = np.concatenate([rng.integers(0, 2048, 400), [0, 0, 2047, 2047, 1, 2046]])
+    o = oracle.Oracle(case, None, threads=16)
+    of, oh = o.update_nodes(xs, ys, f0, h0)
+    np.testing.assert_allclose(f1[:, ys, xs].T, of, rtol=0, atol=2e-6)
+    np.testing.assert_allclose(h1[:, ys, xs].T, oh, rtol=0, atol=2e-6)

@@ -144,6 +144,22 @@ tclbm_status tclbm_moments(tclbm_lattice* lat, double* rho, double* ux, double* 
  * Synchronises the stream. */
 tclbm_status tclbm_diagnostics(tclbm_lattice* lat, double out[TCLBM_NDIAG]);
 
+/* Allocation-free form of the sums of tclbm_diagnostics() (no counterpart in the paper).
+ * For callers that may not allocate device memory when they need the sums -- a serving
+ * loop whose memory is planned up front, code under a fixed memory budget, embedders
+ * that only pass raw device pointers.  Inputs: the lattice's parameters, and device
+ * pointers f, h to FP64 populations in the layout of tclbm_get_populations() (double
+ * [9][ny][nx] each; h may be NULL for athermal lattices), u_snap: NULL or a device
+ * double [2][ny][nx] velocity reference for out[6] (0 when NULL).  out: 8 doubles, on
+ * the device if out_on_device, else on the host (then the call synchronises `stream`).
+ * Block partial sums live in a fixed 65,600-byte file-scope device array held by every
+ * device that loads the library; no cudaMalloc, cudaFree or other allocating call is
+ * made.  Lattices above 67,108,864 nodes are rejected with TCLBM_EINVAL.  The first call
+ * on a device resolves the array's address with that device current; make it before
+ * any stream capture.  All calls share the array: calls that overlap on the GPU race. */
+tclbm_status tclbm_diagnostics_noalloc(const tclbm_params* params, const double* f, const double* h,
+                                       const double* u_snap, double* out, int32_t out_on_device, void* stream);
+
 /* Store the current velocity field as the reference of out[6] in tclbm_diagnostics(). */
 tclbm_status tclbm_snapshot_velocity(tclbm_lattice* lat);
 

@@ -44,6 +44,8 @@ constexpr int kDiagBlock = 256;
 constexpr int kDiagMaxBlocks = 1024;
 }  // namespace
 
+void tclbm::set_last_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
 struct tclbm_lattice {
     tclbm_params prm;
     DevParams dp;

@@ -7,6 +7,9 @@
 #include "tclbm_device.cuh"
 
 namespace tclbm {
+// Sets the thread-local message returned by tclbm_last_error().
+void set_last_error(const char* msg);
+
 cudaError_t launch_step_fp32(int thermal, int correction, int tx, int ty, const DevParams& p, const void* src,
                              void* dst, cudaStream_t s);
 cudaError_t launch_step_bf16(int thermal, int correction, int tx, int ty, const DevParams& p, const void* src,

@@ -202,6 +202,39 @@ def _flush_l2(buf):
     buf.add_(1.0)  # writes 256 MiB, twice the 129 MB L2
 
 
+def profile_run(args):
+    """Step one Rayleigh-Benard-shaped lattice only (for ncu captures of the step kernel)."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1610_07114_gb300 import build as B
+
+    B.build()
+    from paper_1610_07114_gb300 import tclbm
+    from paper_1610_07114_gb300 import workloads as W
+
+    case, fields = W.rayleigh_benard(args.probe_nx, args.probe_ny, Ra=1e4, seed=2, storage=args.storage)
+    lat = tclbm.Lattice(case, fields)
+    if args.tile:
+        lat.set_tile(*args.tile)
+    if args.kernel is not None:
+        lat.set_kernel(args.kernel)
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lat.step(args.probe_steps)
+    e1.record()
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3 / args.probe_steps
+    n = case["nx"] * case["ny"]
+    print(json.dumps({"profile_run": f"rb_{args.probe_nx}x{args.probe_ny}_{args.storage}", "kernel": lat.describe(),
+                      "us_per_step": dt * 1e6, "LU_per_s": n / dt,
+                      "GBs": BYTES_PER_LU[args.storage] * n / dt / 1e9}))
+    lat.close()
+    return 0
+
+
 def bench_gpu(args):
     import torch
 
@@ -368,11 +401,17 @@ def main():
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--profile-run", action="store_true",
+                    help="only step one --probe-nx x --probe-ny lattice --probe-steps times (for ncu)")
+    ap.add_argument("--tile", type=int, nargs=2, default=None, help="override (tx, rows per CTA)")
+    ap.add_argument("--kernel", type=int, default=None, help="step kernel variant: 0 TMA-staged, 1 direct loads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return bench_reference(args)
+    if args.profile_run:
+        return profile_run(args)
     return bench_gpu(args)
 
 

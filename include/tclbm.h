@@ -71,9 +71,9 @@ enum {
     TCLBM_FORCE_ACCEL = 1,       /* F = rho (ax, ay): gravity as a direct force (Section V.D) */
     TCLBM_FORCE_TAYLOR_GREEN = 2 /* F = famp (sin kx sin ky, cos kx cos ky), k = 2 pi / n (Section V.A) */
 };
-/* Population storage.  FP32 stores f_bar and h_bar as they are; the 16-bit formats
- * store the deviation from the rest state (f_bar - f^eq(1, 0, T0), h_bar - h^eq(1, 0, T0))
- * and compute in FP32. */
+/* Population storage.  Every format stores the deviation of f_bar and h_bar from a rest
+ * state near (rho, u, T) = (1, 0, T0) and the kernels collide on those deviations in
+ * FP32; the 16-bit formats round the stored deviations to bfloat16 or half. */
 enum { TCLBM_STORE_FP32 = 0, TCLBM_STORE_BF16 = 1, TCLBM_STORE_FP16 = 2 };
 
 typedef struct {
@@ -187,6 +187,10 @@ const char* tclbm_describe(const tclbm_lattice* lat);
 /* Launch-shape override for tuning: tile width tx (32, 64 or 128 nodes) and rows per
  * CTA ty (>= 4); 0 keeps the library's choice. */
 tclbm_status tclbm_set_tile(tclbm_lattice* lat, int32_t tx, int32_t ty);
+
+/* Step kernel variant: 0 = rows staged into shared memory by the tensor-memory
+ * accelerator (the default), 1 = direct loads.  Both compute bit-identical states. */
+tclbm_status tclbm_set_kernel(tclbm_lattice* lat, int32_t kind);
 
 #ifdef __cplusplus
 }

@@ -2,6 +2,8 @@
 // validation and derived constants, device memory, the step loop (CUDA graphs for
 // short launches), field initialisation, moments, FP64 diagnostics and population
 // transfer kernels.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -69,10 +71,14 @@ struct tclbm_lattice {
     int cur = 0;
     int64_t steps = 0;
     int tx = 0, ty = 0;
+    int kernel = KERNEL_TMA;
+    CUtensorMap maps[2];  // TMA descriptors of the two copies for box width of tx
+    int maps_tx = 0;
+    int* err = nullptr;  // device error word of the step kernels
     char desc[256] = "";
     // CUDA graph of 2 * kGraphPairs step launches (parity preserved)
     cudaGraphExec_t graph = nullptr;
-    int graph_tx = 0, graph_ty = 0;
+    int graph_tx = 0, graph_ty = 0, graph_kernel = -1;
 };
 
 namespace {
@@ -170,6 +176,8 @@ void derive(tclbm_lattice* L) {
     d.Et0 = (float)Etb;
     d.cRT = (float)(2.0 / b * Etb - RTb);
     d.RTp = (float)(p.R * p.T0);
+    d.inv_RTp = (float)(1.0 / (p.R * p.T0));
+    d.inv_w1_fixed = p.visc_law == TCLBM_VISC_W1 ? (float)(1.0 / p.visc) : 0.0f;
     d.inv_Pr = (float)(1.0 / p.Pr);
     d.Pr_m1 = (float)(p.Pr - 1.0);
     d.force_kind = p.force_kind;
@@ -440,10 +448,28 @@ tclbm_status with_storage(int storage, F&& fn) {
     }
 }
 
+tclbm_status ensure_maps(tclbm_lattice* L);
+
+StepLaunch step_launch(tclbm_lattice* L, int src) {
+    StepLaunch k;
+    k.thermal = L->prm.thermal;
+    k.correction = L->prm.correction;
+    k.tx = L->tx;
+    k.ty = L->ty;
+    k.kernel = L->kernel;
+    k.src_map = &L->maps[src];
+    k.err = L->err;
+    return k;
+}
+
 tclbm_status launch_steps(tclbm_lattice* L, int64_t n) {
+    if (n > 0 && L->kernel == KERNEL_TMA) {
+        tclbm_status st = ensure_maps(L);
+        if (st != TCLBM_OK) return st;
+    }
     for (int64_t s = 0; s < n; ++s) {
-        const cudaError_t e = launch_step_kernel(L->prm.storage, L->prm.thermal, L->prm.correction, L->tx, L->ty,
-                                                 L->dp, L->buf[L->cur], L->buf[L->cur ^ 1], L->stream);
+        const cudaError_t e = launch_step_kernel(L->prm.storage, step_launch(L, L->cur), L->dp, L->buf[L->cur],
+                                                 L->buf[L->cur ^ 1], L->stream);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         L->cur ^= 1;
         ++L->steps;
@@ -452,7 +478,11 @@ tclbm_status launch_steps(tclbm_lattice* L, int64_t n) {
 }
 
 tclbm_status build_graph(tclbm_lattice* L) {
-    if (L->graph && L->graph_tx == L->tx && L->graph_ty == L->ty) return TCLBM_OK;
+    if (L->graph && L->graph_tx == L->tx && L->graph_ty == L->ty && L->graph_kernel == L->kernel) return TCLBM_OK;
+    if (L->kernel == KERNEL_TMA) {
+        tclbm_status st = ensure_maps(L);
+        if (st != TCLBM_OK) return st;
+    }
     if (L->graph) {
         cudaGraphExecDestroy(L->graph);
         L->graph = nullptr;
@@ -463,8 +493,8 @@ tclbm_status build_graph(tclbm_lattice* L) {
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         for (int s = 0; s < 2 * kGraphPairs && e == cudaSuccess; ++s)
-            e = launch_step_kernel(L->prm.storage, L->prm.thermal, L->prm.correction, L->tx, L->ty, L->dp,
-                                   L->buf[s & 1], L->buf[(s & 1) ^ 1], cs);
+            e = launch_step_kernel(L->prm.storage, step_launch(L, s & 1), L->dp, L->buf[s & 1], L->buf[(s & 1) ^ 1],
+                                   cs);
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = e2;
     }
@@ -477,6 +507,48 @@ tclbm_status build_graph(tclbm_lattice* L) {
     }
     L->graph_tx = L->tx;
     L->graph_ty = L->ty;
+    L->graph_kernel = L->kernel;
+    return TCLBM_OK;
+}
+
+// TMA descriptors of both copies: 3-D (x, y, plane), box (tx + 2M, 1, planes).
+tclbm_status ensure_maps(tclbm_lattice* L) {
+    if (L->maps_tx == L->tx) return TCLBM_OK;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return fail(TCLBM_ECUDA, "cuTensorMapEncodeTiled is not available");
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const CUtensorMapDataType dt = L->prm.storage == TCLBM_STORE_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : L->prm.storage == TCLBM_STORE_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)L->dp.pitch, (cuuint64_t)L->prm.ny, (cuuint64_t)L->nplanes};
+    const cuuint64_t strides[2] = {(cuuint64_t)L->dp.pitch * L->elem, (cuuint64_t)L->dp.plane * L->elem};
+    const cuuint32_t box[3] = {(cuuint32_t)tma_box_width(L->prm.storage, L->tx), 1u, (cuuint32_t)L->nplanes};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    for (int b = 0; b < 2; ++b) {
+        const CUresult r = encode(&L->maps[b], dt, 3, L->buf[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(TCLBM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    L->maps_tx = L->tx;
+    return TCLBM_OK;
+}
+
+// Error word of the step kernels (a bounded wait expired): ETIMEOUT once, then cleared.
+tclbm_status check_kernel_error(tclbm_lattice* L) {
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, L->err, sizeof v, cudaMemcpyDeviceToHost, L->stream));
+    CK(cudaStreamSynchronize(L->stream));
+    if (v) {
+        CK(cudaMemsetAsync(L->err, 0, sizeof(int), L->stream));
+        return fail(TCLBM_ETIMEOUT, "a step kernel's pipeline wait expired (%d)", v);
+    }
     return TCLBM_OK;
 }
 
@@ -527,7 +599,8 @@ tclbm_status tclbm_create(const tclbm_params* params, tclbm_alloc_fn alloc, tclb
     L->tables = (float*)dev_alloc(L, L->tables_bytes);
     L->diag = (double*)dev_alloc(L, L->diag_bytes);
     L->stage = (double*)dev_alloc(L, L->stage_bytes);
-    if (!L->buf[0] || !L->buf[1] || !L->tables || !L->diag || !L->stage) {
+    L->err = (int*)dev_alloc(L, 256);
+    if (!L->buf[0] || !L->buf[1] || !L->tables || !L->diag || !L->stage || !L->err) {
         tclbm_destroy(L);
         return fail(TCLBM_ENOMEM, "device allocation of %zu bytes failed", tclbm_state_bytes(params));
     }
@@ -560,10 +633,21 @@ tclbm_status tclbm_create(const tclbm_params* params, tclbm_alloc_fn alloc, tclb
         L->dp.cy = L->tables + 2 * nx + ny;
     }
     cudaError_t e = cudaMemsetAsync(L->buf[0], 0, L->buf_bytes, L->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->err, 0, 256, L->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(L->buf[1], 0, L->buf_bytes, L->stream);
     if (e != cudaSuccess) {
         tclbm_destroy(L);
         return cuda_fail(e, "state clear");
+    }
+    {
+        // dynamic shared-memory limits of the TMA kernels, set before any launch or capture
+        const cudaError_t pe = params->storage == TCLBM_STORE_FP32   ? prepare_step_fp32()
+                               : params->storage == TCLBM_STORE_BF16 ? prepare_step_bf16()
+                                                                     : prepare_step_fp16();
+        if (pe != cudaSuccess) {
+            tclbm_destroy(L);
+            return cuda_fail(pe, "step kernel attributes");
+        }
     }
     snprintf(L->desc, sizeof L->desc, "unset");
     *out = L;
@@ -580,6 +664,7 @@ tclbm_status tclbm_destroy(tclbm_lattice* L) {
     dev_free(L, L->diag, L->diag_bytes);
     dev_free(L, L->usnap, L->usnap_bytes);
     dev_free(L, L->stage, L->stage_bytes);
+    dev_free(L, L->err, 256);
     delete L;
     return TCLBM_OK;
 }
@@ -603,11 +688,17 @@ tclbm_status tclbm_set_tile(tclbm_lattice* L, int32_t tx, int32_t ty) {
     return TCLBM_OK;
 }
 
+tclbm_status tclbm_set_kernel(tclbm_lattice* L, int32_t kind) {
+    if (!L) return fail(TCLBM_EINVAL, "lattice is NULL");
+    if (kind != KERNEL_TMA && kind != KERNEL_DIRECT) return fail(TCLBM_EINVAL, "kernel kind must be 0 or 1");
+    L->kernel = kind;
+    return TCLBM_OK;
+}
+
 const char* tclbm_describe(const tclbm_lattice* L) {
     if (!L) return "";
     tclbm_lattice* M = const_cast<tclbm_lattice*>(L);
-    describe_step_kernel(L->prm.storage, L->prm.thermal, L->prm.correction, L->tx, L->ty, L->dp, M->desc,
-                         sizeof M->desc);
+    describe_step_kernel(L->prm.storage, step_launch(M, 0), L->dp, M->desc, sizeof M->desc);
     return L->desc;
 }
 
@@ -689,7 +780,7 @@ tclbm_status tclbm_moments(tclbm_lattice* L, double* rho, double* ux, double* uy
             if (out[k])
                 CK(cudaMemcpyAsync(out[k], dst[k], n * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
     CK(cudaStreamSynchronize(L->stream));
-    return TCLBM_OK;
+    return check_kernel_error(L);
 }
 
 tclbm_status tclbm_snapshot_velocity(tclbm_lattice* L) {
@@ -732,6 +823,8 @@ tclbm_status tclbm_diagnostics(tclbm_lattice* L, double out[TCLBM_NDIAG]) {
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(out, res, TCLBM_NDIAG * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
     CK(cudaStreamSynchronize(L->stream));
+    tclbm_status ks = check_kernel_error(L);
+    if (ks != TCLBM_OK) return ks;
     for (int k = 0; k < TCLBM_NDIAG; ++k)
         if (!std::isfinite(out[k])) return fail(TCLBM_ENONFINITE, "non-finite diagnostic %d", k);
     return TCLBM_OK;
@@ -767,7 +860,7 @@ tclbm_status tclbm_get_populations(tclbm_lattice* L, double* f, double* h, int32
     if (tmp) dev_free(L, tmp, 2 * bytes);
     if (st != TCLBM_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "get_populations");
-    return TCLBM_OK;
+    return check_kernel_error(L);
 }
 
 tclbm_status tclbm_set_populations(tclbm_lattice* L, const double* f, const double* h, int32_t on_device) {

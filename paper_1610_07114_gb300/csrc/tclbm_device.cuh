@@ -37,7 +37,8 @@ struct DevParams {
     float visc, w2, w3, w4;
     int bgk;
     float R, T0, b, two_over_b, inv_R, inv_Pr, Pr_m1;
-    float RTp;            // R T0 (the athermal temperature)
+    float RTp, inv_RTp;   // R T0 (the athermal temperature) and its inverse
+    float inv_w1_fixed;   // 1 / w1 for VISC_W1
     float RT0, Et0, cRT;  // rest state of the deviations (exact floats); cRT = (2/b) Et0 - RT0
     int force_kind;
     float ax, ay, famp;
@@ -64,26 +65,37 @@ struct Store;
 template <>
 struct Store<float> {
     static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float ld_smem(const float* p) { return *p; }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 };
 template <>
 struct Store<__half> {
     static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_smem(const __half* p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 };
 template <>
 struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float ld_smem(const __nv_bfloat16* p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
 // ---------------------------------------------------------------- node arithmetic
 
+// 1/x from the hardware approximation refined by one Newton step (relative error a few
+// 1e-8); deterministic, so every inlined copy returns the same bits for the same x.
+__device__ __forceinline__ float rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return __fmul_rn(r, __fmaf_rn(-x, r, 2.0f));
+}
+
 // Node state after Eq. 20, kept both whole and as deviations from the rest state
 // (rho0 = 1, RT0 = R T0, Et0 = b RT0 / 2): Et = sum h_bar / rho is the total energy per
 // unit mass and RT = (2/b)(Et - u^2/2).
 struct Macro {
-    float rho, drho, ux, uy, ax, ay, RT, dRT, Et, dEt;
+    float rho, drho, irho, ux, uy, ax, ay, RT, dRT, Et, dEt;
 };
 
 __device__ __forceinline__ void force_at(const DevParams& p, int x, int y, float rho, float& Fx, float& Fy) {
@@ -117,7 +129,8 @@ __device__ __forceinline__ Macro macro_of(const DevParams& p, const float* f, co
     const float jy = __fadd_rn(__fadd_rn(__fsub_rn(f[2], f[4]), __fsub_rn(f[5], f[7])), __fsub_rn(f[6], f[8]));
     float Fx, Fy;
     force_at(p, x, y, m.rho, Fx, Fy);
-    const float irho = __frcp_rn(m.rho);
+    const float irho = __frcp_rn(m.rho);  // correctly rounded: 1/rho feeds u, whose bias would accumulate
+    m.irho = irho;
     m.ux = __fmul_rn(__fmaf_rn(0.5f, Fx, jx), irho);
     m.uy = __fmul_rn(__fmaf_rn(0.5f, Fy, jy), irho);
     m.ax = __fmul_rn(Fx, irho);
@@ -212,15 +225,14 @@ __device__ __forceinline__ void source(float rho, float ux, float uy, float ax, 
         2.0f * ax * ux * uy * uy + 2.0f * ay * uy * ux * ux, o);
 }
 
-__device__ __forceinline__ float omega1(const DevParams& p, float rho, float RT) {
-    float inv;
+// Eq. 29: 1/w1 = mu/p + 1/2 with p = rho R T; returns mu/p (= 1/w1 - 1/2).
+__device__ __forceinline__ float mu_over_p(const DevParams& p, float irho, float RT) {
     switch (p.visc_law) {
-        case VISC_NU: inv = p.visc / RT + 0.5f; break;
-        case VISC_MU: inv = p.visc / (rho * RT) + 0.5f; break;
-        case VISC_MU_PROP_T: inv = p.visc / (rho * p.RTp) + 0.5f; break;
-        default: return p.visc;
+        case VISC_NU: return p.visc * rcp(RT);
+        case VISC_MU: return p.visc * irho * rcp(RT);
+        case VISC_MU_PROP_T: return p.visc * irho * p.inv_RTp;
+        default: return p.inv_w1_fixed - 0.5f;
     }
-    return 1.0f / inv;
 }
 
 // One node's collision on deviations: (df, dh) at time t -> deviations of
@@ -230,10 +242,11 @@ template <bool THERMAL>
 __device__ __forceinline__ void collide(const DevParams& p, const float* f, const float* h, const Macro& m,
                                         float dx, float dy, float* fo, float* ho) {
     const float rho = m.rho, drho = m.drho, ux = m.ux, uy = m.uy, ax = m.ax, ay = m.ay;
-    const float irho = 1.0f / rho;
+    const float irho = m.irho;
     const float RT0 = p.RT0, RT = m.RT, dRT = m.dRT;
     const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy, uu = ux2 + uy2;
-    const float w1 = omega1(p, rho, RT);
+    const float mup = mu_over_p(p, irho, RT);
+    const float w1 = p.visc_law == VISC_W1 ? p.visc : rcp(mup + 0.5f);
     const float w2 = p.bgk ? w1 : p.w2, w3 = p.bgk ? w1 : p.w3, w4 = p.bgk ? w1 : p.w4;
 
     // raw moments (Eq. 1) of the deviations; the rest state contributes 1, RT0, RT0^2
@@ -304,7 +317,7 @@ __device__ __forceinline__ void collide(const DevParams& p, const float* f, cons
         float g[9];
         eq3(rho, 0.0f, 0.0f, 0.0f, dEg, dNg, dPig, dM21g, dM12g, dM22g, g);
         // 1/w_h = (1/w1 - 1/2)/Pr + 1/2 (lambda = mu c_p / Pr); 1/tau_hf = (Pr - 1) w1
-        const float wh = 1.0f / ((1.0f / w1 - 0.5f) * p.inv_Pr + 0.5f);
+        const float wh = rcp(mup * p.inv_Pr + 0.5f);
         const float kc = p.Pr_m1 * w1 * (1.0f - 0.5f * wh);
         float he[9];
         dheq(p, rho, drho, ux, uy, RT, dRT, m.Et, m.dEt, he);
@@ -508,7 +521,7 @@ __device__ __forceinline__ void store_node(const DevParams& p, ST* __restrict__ 
 
 // Variant without the correction term: no neighbour moments, one row at a time.
 template <int TX, bool THERMAL, class ST>
-__global__ void __launch_bounds__(TX) tclbm_step_plain(const DevParams p, const ST* __restrict__ src,
+__global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_plain(const DevParams p, const ST* __restrict__ src,
                                                        ST* __restrict__ dst, int rows_per_cta) {
     const int x = blockIdx.x * TX + threadIdx.x;
     if (x >= p.nx) return;
@@ -528,7 +541,7 @@ __global__ void __launch_bounds__(TX) tclbm_step_plain(const DevParams p, const 
 // x-derivative from a three-row ring of u_x(1-theta) in shared memory with a
 // two-column halo on each side (computed by four designated threads).
 template <int TX, class ST>
-__global__ void __launch_bounds__(TX) tclbm_step_corr(const DevParams p, const ST* __restrict__ src,
+__global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_corr(const DevParams p, const ST* __restrict__ src,
                                                       ST* __restrict__ dst, int rows_per_cta) {
     __shared__ float ring[3][TX + 4];
     const int tid = threadIdx.x;

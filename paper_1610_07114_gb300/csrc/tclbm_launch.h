@@ -4,27 +4,41 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <cuda.h>
+
 #include "tclbm_device.cuh"
 
 namespace tclbm {
 // Sets the thread-local message returned by tclbm_last_error().
 void set_last_error(const char* msg);
 
-cudaError_t launch_step_fp32(int thermal, int correction, int tx, int ty, const DevParams& p, const void* src,
-                             void* dst, cudaStream_t s);
-cudaError_t launch_step_bf16(int thermal, int correction, int tx, int ty, const DevParams& p, const void* src,
-                             void* dst, cudaStream_t s);
-cudaError_t launch_step_fp16(int thermal, int correction, int tx, int ty, const DevParams& p, const void* src,
-                             void* dst, cudaStream_t s);
+// Kernel variants: the TMA-fed ring (default) and the direct-load marching kernel.
+enum { KERNEL_TMA = 0, KERNEL_DIRECT = 1 };
 
-inline cudaError_t launch_step_kernel(int storage, int thermal, int correction, int tx, int ty, const DevParams& p,
-                                      const void* src, void* dst, cudaStream_t s) {
+struct StepLaunch {
+    int thermal, correction, tx, ty, kernel;
+    const CUtensorMap* src_map;  // tensor map of the source copy (KERNEL_TMA)
+    int* err;                    // device error word (bounded waits that expired)
+};
+
+cudaError_t launch_step_fp32(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s);
+cudaError_t launch_step_bf16(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s);
+cudaError_t launch_step_fp16(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s);
+cudaError_t prepare_step_fp32();
+cudaError_t prepare_step_bf16();
+cudaError_t prepare_step_fp16();
+
+inline cudaError_t launch_step_kernel(int storage, const StepLaunch& k, const DevParams& p, const void* src,
+                                      void* dst, cudaStream_t s) {
     switch (storage) {
-        case 0: return launch_step_fp32(thermal, correction, tx, ty, p, src, dst, s);
-        case 1: return launch_step_bf16(thermal, correction, tx, ty, p, src, dst, s);
-        default: return launch_step_fp16(thermal, correction, tx, ty, p, src, dst, s);
+        case 0: return launch_step_fp32(k, p, src, dst, s);
+        case 1: return launch_step_bf16(k, p, src, dst, s);
+        default: return launch_step_fp16(k, p, src, dst, s);
     }
 }
+
+// Box width (elements) of the TMA row copy for a strip of tx columns.
+inline int tma_box_width(int storage, int tx) { return tx + 2 * (storage == 0 ? 4 : 8); }
 
 inline dim3 step_grid(const DevParams& p, int tx, int ty) {
     int nseg = p.ny / ty;
@@ -32,12 +46,13 @@ inline dim3 step_grid(const DevParams& p, int tx, int ty) {
     return dim3((unsigned)((p.nx + tx - 1) / tx), (unsigned)nseg, 1);
 }
 
-inline void describe_step_kernel(int storage, int thermal, int correction, int tx, int ty, const DevParams& p,
-                                 char* out, size_t len) {
+inline void describe_step_kernel(int storage, const StepLaunch& k, const DevParams& p, char* out, size_t len) {
     const char* st = storage == 0 ? "float" : (storage == 1 ? "bf16" : "half");
-    const dim3 g = step_grid(p, tx, ty);
-    snprintf(out, len, "%s<%d,%s%s> grid (%u, %u) block (%d) rows/cta %d",
-             (thermal && correction) ? "tclbm_step_corr" : "tclbm_step_plain", tx,
-             (thermal && correction) ? "" : (thermal ? "thermal," : "athermal,"), st, g.x, g.y, tx, ty);
+    const dim3 g = step_grid(p, k.tx, k.ty);
+    const bool corr = k.thermal && k.correction;
+    const char* base = k.kernel == KERNEL_TMA ? (corr ? "tclbm_step_tma_corr" : "tclbm_step_tma_plain")
+                                              : (corr ? "tclbm_step_corr" : "tclbm_step_plain");
+    snprintf(out, len, "%s<%d,%s%s> grid (%u, %u) block (%d) rows/cta %d", base, k.tx,
+             corr ? "" : (k.thermal ? "thermal," : "athermal,"), st, g.x, g.y, k.tx, k.ty);
 }
 }  // namespace tclbm

@@ -4,4 +4,5 @@ namespace tclbm {
 using ST = __nv_bfloat16;
 }
 #define LAUNCH_FN launch_step_bf16
+#define PREPARE_FN prepare_step_bf16
 #include "tclbm_step_inst.cuh"

@@ -4,4 +4,5 @@ namespace tclbm {
 using ST = __half;
 }
 #define LAUNCH_FN launch_step_fp16
+#define PREPARE_FN prepare_step_fp16
 #include "tclbm_step_inst.cuh"

@@ -4,4 +4,5 @@ namespace tclbm {
 using ST = float;
 }
 #define LAUNCH_FN launch_step_fp32
+#define PREPARE_FN prepare_step_fp32
 #include "tclbm_step_inst.cuh"

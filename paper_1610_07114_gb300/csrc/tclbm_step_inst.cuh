@@ -3,30 +3,65 @@
 #include <cstdio>
 
 #include "tclbm_launch.h"
+#include "tclbm_tma.cuh"
 
 namespace tclbm {
 
+template <class K>
+static cudaError_t allow_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 template <int TX>
-static cudaError_t launch_tx(int thermal, int correction, int ty, const DevParams& p, const void* src, void* dst,
-                             cudaStream_t s) {
-    const dim3 grid = step_grid(p, TX, ty);
+static cudaError_t launch_tx(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s) {
+    const dim3 grid = step_grid(p, TX, k.ty);
     const ST* in = static_cast<const ST*>(src);
     ST* out = static_cast<ST*>(dst);
-    if (thermal && correction)
-        tclbm_step_corr<TX, ST><<<grid, TX, 0, s>>>(p, in, out, ty);
-    else if (thermal)
-        tclbm_step_plain<TX, true, ST><<<grid, TX, 0, s>>>(p, in, out, ty);
-    else
-        tclbm_step_plain<TX, false, ST><<<grid, TX, 0, s>>>(p, in, out, ty);
+    const bool corr = k.thermal && k.correction;
+    if (k.kernel == KERNEL_TMA) {
+        if (corr) {
+            const size_t sm = tma_smem_bytes<TX, true, ST>(true);
+            tclbm_step_tma_corr<TX, ST><<<grid, TX, sm, s>>>(p, *k.src_map, in, out, k.ty, k.err);
+        } else if (k.thermal) {
+            const size_t sm = tma_smem_bytes<TX, true, ST>(false);
+            tclbm_step_tma_plain<TX, true, ST><<<grid, TX, sm, s>>>(p, *k.src_map, in, out, k.ty, k.err);
+        } else {
+            const size_t sm = tma_smem_bytes<TX, false, ST>(false);
+            tclbm_step_tma_plain<TX, false, ST><<<grid, TX, sm, s>>>(p, *k.src_map, in, out, k.ty, k.err);
+        }
+    } else {
+        if (corr)
+            tclbm_step_corr<TX, ST><<<grid, TX, 0, s>>>(p, in, out, k.ty);
+        else if (k.thermal)
+            tclbm_step_plain<TX, true, ST><<<grid, TX, 0, s>>>(p, in, out, k.ty);
+        else
+            tclbm_step_plain<TX, false, ST><<<grid, TX, 0, s>>>(p, in, out, k.ty);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t LAUNCH_FN(int thermal, int correction, int tx, int ty, const DevParams& p, const void* src, void* dst,
-                      cudaStream_t s) {
-    switch (tx) {
-        case 32: return launch_tx<32>(thermal, correction, ty, p, src, dst, s);
-        case 64: return launch_tx<64>(thermal, correction, ty, p, src, dst, s);
-        default: return launch_tx<128>(thermal, correction, ty, p, src, dst, s);
+template <int TX>
+static cudaError_t prepare_tx() {
+    cudaError_t e = allow_smem(tclbm_step_tma_corr<TX, ST>, tma_smem_bytes<TX, true, ST>(true));
+    if (e == cudaSuccess) e = allow_smem(tclbm_step_tma_plain<TX, true, ST>, tma_smem_bytes<TX, true, ST>(false));
+    if (e == cudaSuccess) e = allow_smem(tclbm_step_tma_plain<TX, false, ST>, tma_smem_bytes<TX, false, ST>(false));
+    return e;
+}
+
+// Dynamic shared-memory limits of every TMA kernel of this format (current device).
+cudaError_t PREPARE_FN() {
+    cudaError_t e = prepare_tx<32>();
+    if (e == cudaSuccess) e = prepare_tx<64>();
+    if (e == cudaSuccess) e = prepare_tx<128>();
+    return e;
+}
+
+cudaError_t LAUNCH_FN(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s) {
+    switch (k.tx) {
+        case 32: return launch_tx<32>(k, p, src, dst, s);
+        case 64: return launch_tx<64>(k, p, src, dst, s);
+        default: return launch_tx<128>(k, p, src, dst, s);
     }
 }
 

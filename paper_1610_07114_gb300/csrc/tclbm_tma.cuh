@@ -1,0 +1,415 @@
+// tclbm_tma.cuh -- the fused step with TMA-fed row staging (sm_103a).
+//
+// One thread per CTA streams whole source rows -- all 9 or 18 planes of columns
+// [x0 - M, x0 + TX + M) -- from HBM into an 8-slot shared-memory ring with
+// cp.async.bulk.tensor (one 3-D box per row), signalling an mbarrier per slot.  The
+// compute threads pull their node's populations from the ring (f_q(x, t+1) =
+// f_out_q(x - e_q, t) is a shifted shared-memory read), collide, and store their own
+// node to the destination copy.  Rows are staged several rows ahead of use, so HBM
+// latency is hidden by the copy engine rather than by registers or occupancy.
+//
+// The ring holds source rows r-2 .. r+3 (r+5 with 8 slots) while output row r is
+// processed: the pull of row r needs r-1..r+1, a top-wall node also reads its interior
+// neighbour's pulls (r-2..r), the correction-term lookahead needs row r+1 (sources up
+// to r+2) and a bottom-wall node the one-sided stencil's row 2 (sources up to 3).
+// A launch that finds the error word set returns at once.  Periodic wrap in x: strips whose
+// box crosses x = 0 or x = nx patch the wrapped columns from global memory after the
+// row lands; in y the producer requests the wrapped (or clamped) row directly.
+//
+// Every wait is bounded by the global timer; on expiry the CTA records an error code,
+// drains its own outstanding copies (again bounded) and returns.
+#pragma once
+
+#include <cuda.h>
+
+#include "tclbm_device.cuh"
+
+namespace tclbm {
+
+constexpr long long kWaitNs = 1000000000LL;  // 1 s per wait
+
+// Ring slots: FP32 rows are twice the bytes of 16-bit rows, so FP32 keeps 6 slots
+// (prefetch one row beyond the five in use) to leave room for more CTAs per SM.
+template <class ST>
+struct RingSlots {
+    static constexpr int N = sizeof(ST) == 4 ? 6 : 8;
+};
+
+__device__ __forceinline__ long long globaltimer_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait: true when the phase with this parity completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long deadline = globaltimer_ns() + kWaitNs;
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer_ns() > deadline) return false;
+    return true;
+}
+
+// Row copy: box (BOXW, 1, NP) at (x, y, 0) into `dst`, completing on `bar`.
+__device__ __forceinline__ void tma_row(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                        uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(0), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <class ST>
+struct TmaGeom {
+    static constexpr int M = 16 / (int)sizeof(ST);  // halo columns each side; keeps x * size on 16 B
+};
+
+// Shared-memory pull of node column `xi` (index in the box) for target row t, whose
+// source rows t-1, t, t+1 sit at ring slots sm1, s0, sp1.
+template <bool THERMAL, class ST, int BOXW, int SLOT>
+__device__ __forceinline__ void pull_ring(const ST* ring, int sm1, int s0, int sp1, int xi, float* f, float* h) {
+    // plane q comes from source row t - e_qy and column x - e_qx
+    const ST* r_m = ring + sm1 * SLOT;  // row t-1 (e_y = +1: planes 2, 5, 6)
+    const ST* r_0 = ring + s0 * SLOT;   // row t   (planes 0, 1, 3)
+    const ST* r_p = ring + sp1 * SLOT;  // row t+1 (planes 4, 7, 8)
+    auto ld = [](const ST* p) { return Store<ST>::ld_smem(p); };
+    f[0] = ld(r_0 + 0 * BOXW + xi);
+    f[1] = ld(r_0 + 1 * BOXW + xi - 1);
+    f[2] = ld(r_m + 2 * BOXW + xi);
+    f[3] = ld(r_0 + 3 * BOXW + xi + 1);
+    f[4] = ld(r_p + 4 * BOXW + xi);
+    f[5] = ld(r_m + 5 * BOXW + xi - 1);
+    f[6] = ld(r_m + 6 * BOXW + xi + 1);
+    f[7] = ld(r_p + 7 * BOXW + xi + 1);
+    f[8] = ld(r_p + 8 * BOXW + xi - 1);
+    if (THERMAL) {
+        h[0] = ld(r_0 + 9 * BOXW + xi);
+        h[1] = ld(r_0 + 10 * BOXW + xi - 1);
+        h[2] = ld(r_m + 11 * BOXW + xi);
+        h[3] = ld(r_0 + 12 * BOXW + xi + 1);
+        h[4] = ld(r_p + 13 * BOXW + xi);
+        h[5] = ld(r_m + 14 * BOXW + xi - 1);
+        h[6] = ld(r_m + 15 * BOXW + xi + 1);
+        h[7] = ld(r_p + 16 * BOXW + xi + 1);
+        h[8] = ld(r_p + 17 * BOXW + xi - 1);
+    }
+}
+
+// Pipeline bookkeeping shared by the two kernels below.
+template <int TX, bool THERMAL, class ST>
+struct RowRing {
+    static constexpr int M = TmaGeom<ST>::M;
+    static constexpr int BOXW = TX + 2 * M;
+    static constexpr int NP = THERMAL ? 18 : 9;
+    static constexpr uint32_t ROW_BYTES = (uint32_t)(BOXW * NP * sizeof(ST));     // bytes one copy delivers
+    static constexpr uint32_t SLOT_BYTES = (ROW_BYTES + 127u) / 128u * 128u;       // slots start 128-byte aligned
+    static constexpr int SLOT_ELEMS = (int)(SLOT_BYTES / sizeof(ST));
+    static constexpr int NS = RingSlots<ST>::N;
+    static constexpr size_t RING_BYTES = (size_t)NS * SLOT_BYTES;
+
+    ST* ring;
+    uint64_t* bar;
+    const CUtensorMap* map;
+    int s_first, s_last;  // source rows this CTA stages
+    int issued_to;        // highest source row issued
+    int ready_to;         // highest source row waited for (and patched)
+    bool patch;           // strip box crosses x = 0 or x = nx on a periodic x axis
+    int xb;               // logical column of box index 0
+
+    __device__ __forceinline__ int slot(int s) const { return (s - s_first) % NS; }
+    __device__ __forceinline__ uint32_t parity(int s) const { return (uint32_t)(((s - s_first) / NS) & 1); }
+    __device__ __forceinline__ int phys_row(const DevParams& p, int s) const {
+        if (p.yper) return ((s % p.ny) + p.ny) % p.ny;
+        return s < 0 ? 0 : (s >= p.ny ? p.ny - 1 : s);
+    }
+    // thread 0 only
+    __device__ __forceinline__ void issue(const DevParams& p, int s) {
+        tma_row(ring + (size_t)slot(s) * SLOT_ELEMS, map, bar + slot(s), xb, phys_row(p, s), ROW_BYTES);
+        issued_to = s;
+    }
+    // every thread: make sources up to `s_need` available; false on timeout
+    __device__ __forceinline__ bool acquire(const DevParams& p, const ST* __restrict__ src, int s_need) {
+        if (s_need > s_last) s_need = s_last;
+        bool ok = true;
+        bool patched = false;
+        while (ready_to < s_need) {
+            const int s = ready_to + 1;
+            ok = mbar_wait(bar + slot(s), parity(s)) && ok;
+            if (patch) {
+                // wrapped columns of a periodic x axis, straight from global memory: the
+                // box columns left of x = 0 (n_left of them) and right of nx - 1 (n_right)
+                ST* row = ring + (size_t)slot(s) * SLOT_ELEMS;
+                const ST* srow = src + (long long)phys_row(p, s) * p.pitch;
+                const int n_left = xb < 0 ? -xb : 0;
+                const int c_right = p.nx - xb;  // first box column with x >= nx
+                const int n_right = c_right < BOXW ? BOXW - c_right : 0;
+                const int ncol = n_left + n_right;
+                for (int i = threadIdx.x; i < ncol * NP; i += blockDim.x) {
+                    const int q = i / ncol, k = i - q * ncol;
+                    const int c = k < n_left ? k : c_right + (k - n_left);
+                    int xp = xb + c;
+                    xp = xp < 0 ? xp + p.nx : xp - p.nx;
+                    if (xp < 0 || xp >= p.nx) xp = ((xp % p.nx) + p.nx) % p.nx;  // nx smaller than the halo
+                    row[q * BOXW + c] = srow[(long long)q * p.plane + xp];
+                }
+                patched = true;
+            }
+            ready_to = s;
+        }
+        if (patched) __syncthreads();
+        return ok;
+    }
+    // every thread, after a timeout was agreed on: wait (bounded) for copies still in flight
+    __device__ __forceinline__ void drain() {
+        for (int s = ready_to + 1; s <= issued_to; ++s) mbar_wait(bar + slot(s), parity(s));
+    }
+};
+
+// Streamed populations of the node at box index xi, logical column xl, physical
+// (x, y), target row t, with its wall scheme applied; the wall neighbour is read from
+// the ring as well (rows t +- 1 .. t +- 2).
+template <int TX, bool THERMAL, class ST>
+__device__ __forceinline__ void load_node_ring(const DevParams& p, const RowRing<TX, THERMAL, ST>& R, int t, int xi,
+                                               int x, int y, float* f, float* h) {
+    using RR = RowRing<TX, THERMAL, ST>;
+    pull_ring<THERMAL, ST, RR::BOXW, RR::SLOT_ELEMS>(R.ring, R.slot(t - 1), R.slot(t), R.slot(t + 1), xi, f, h);
+    const int side = wall_side_of(p, x, y);
+    if (side >= 0) {
+        const int nxv = side == SIDE_XM ? 1 : (side == SIDE_XP ? -1 : 0);
+        const int nyv = side == SIDE_YM ? 1 : (side == SIDE_YP ? -1 : 0);
+        const int tn = t + nyv;
+        float ff[9], hf[9];
+        pull_ring<THERMAL, ST, RR::BOXW, RR::SLOT_ELEMS>(R.ring, R.slot(tn - 1), R.slot(tn), R.slot(tn + 1), xi + nxv, ff,
+                                                         hf);
+        wall_rebuild<THERMAL>(p, side, x, y, f, h, ff, hf);
+    }
+}
+
+template <int TX, bool THERMAL, class ST>
+__device__ __forceinline__ void ring_setup(RowRing<TX, THERMAL, ST>& R, unsigned char* smem, const CUtensorMap* map,
+                                           int x0, int s_first, int s_last, const DevParams& p) {
+    using RR = RowRing<TX, THERMAL, ST>;
+    R.ring = reinterpret_cast<ST*>(smem);
+    R.bar = reinterpret_cast<uint64_t*>(smem + RR::RING_BYTES);  // 8 barrier words reserved
+    R.map = map;
+    R.s_first = s_first;
+    R.s_last = s_last;
+    R.issued_to = s_first - 1;
+    R.ready_to = s_first - 1;
+    R.xb = x0 - RR::M;
+    R.patch = p.xper && (R.xb < 0 || R.xb + RR::BOXW > p.nx);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < RR::NS; ++k) mbar_init(R.bar + k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int last = s_first + RR::NS - 1 < s_last ? s_first + RR::NS - 1 : s_last;
+        for (int s = s_first; s <= last; ++s) R.issue(p, s);
+    }
+}
+
+// thread 0: reuse the slot of a source row nobody reads any more (after a barrier)
+template <int TX, bool THERMAL, class ST>
+__device__ __forceinline__ void ring_refill(RowRing<TX, THERMAL, ST>& R, const DevParams& p, int s_free) {
+    const int s_new = s_free + RowRing<TX, THERMAL, ST>::NS;
+    if (threadIdx.x == 0 && s_free >= R.s_first && s_new <= R.s_last && s_new > R.issued_to) {
+        // generic-proxy reads (and wrap patches) of this slot happened before the barrier
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        R.issue(p, s_new);
+    }
+}
+
+// Without the correction term (athermal, or thermal with C off).
+template <int TX, bool THERMAL, class ST>
+__global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_plain(const DevParams p, const __grid_constant__ CUtensorMap map,
+                                                           const ST* __restrict__ src, ST* __restrict__ dst,
+                                                           int rows_per_cta, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    using RR = RowRing<TX, THERMAL, ST>;
+    RR R;
+    if (*(volatile int*)err) return;  // an earlier launch gave up: do not queue more waits
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX;
+    const int nseg = gridDim.y;
+    const int y0 = blockIdx.y * rows_per_cta;
+    const int y1 = (blockIdx.y == nseg - 1) ? p.ny : y0 + rows_per_cta;
+    // output row r pulls sources r-1..r+1; a wall row's neighbour reaches r-2 / r+2
+    ring_setup<TX, THERMAL, ST>(R, smem, &map, x0, y0 - 2, y1 + 1, p);
+    const int x = x0 + tid;
+    const bool owns = x < p.nx;
+    const int xi = tid + RR::M;
+    for (int r = y0; r < y1; ++r) {
+        const bool ok = R.acquire(p, src, r + 2);
+        if (owns) {
+            float f[9], h[9], fo[9], ho[9];
+            load_node_ring<TX, THERMAL, ST>(p, R, r, xi, x, r, f, h);
+            const Macro m = macro_of<THERMAL>(p, f, h, x, r);
+            collide<THERMAL>(p, f, h, m, 0.0f, 0.0f, fo, ho);
+            store_node<ST>(p, dst, x, r, fo, ho, THERMAL);
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(err, 1);
+            R.drain();
+            return;
+        }
+        ring_refill<TX, THERMAL, ST>(R, p, r - 2);
+    }
+}
+
+// With the correction term: lookahead of one row for the same-time moments, x halo of
+// two columns each side from the ring, the x-derivative through a three-row ring of
+// u_x (1 - theta) in shared memory.
+template <int TX, class ST>
+__global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_corr(const DevParams p, const __grid_constant__ CUtensorMap map,
+                                                          const ST* __restrict__ src, ST* __restrict__ dst,
+                                                          int rows_per_cta, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    using RR = RowRing<TX, true, ST>;
+    RR R;
+    if (*(volatile int*)err) return;  // an earlier launch gave up: do not queue more waits
+    float(*phix)[TX + 4] = reinterpret_cast<float(*)[TX + 4]>(smem + RR::RING_BYTES + 8 * sizeof(uint64_t));
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX;
+    const int nx = p.nx, ny = p.ny;
+    const int nseg = gridDim.y;
+    const int y0 = blockIdx.y * rows_per_cta;
+    const int y1 = (blockIdx.y == nseg - 1) ? ny : y0 + rows_per_cta;
+    const bool ywall = !p.yper;
+    // sources: the phi_y of row y0-1 needs y0-2; the lookahead of row y1 needs y1+1;
+    // the bottom wall's one-sided stencil needs row 3 (inside the first ring fill)
+    const int s_first = y0 - 2;
+    int s_last = y1 + 1;
+    if (ywall && y0 == 0 && s_last < 3) s_last = 3;
+    ring_setup<TX, true, ST>(R, smem, &map, x0, s_first, s_last, p);
+
+    const int xl = x0 + tid;  // logical column of this thread
+    const bool owns = xl < nx;
+    const int xown = p.xper ? (xl % nx) : xl;
+    const bool own_valid = p.xper || owns;
+    const int xi = tid + RR::M;
+    // the four halo slots (columns x0-2, x0-1, x0+TX, x0+TX+1) go to lanes 0..3 of the last warp
+    int hslot = -1, xh = 0, xih = 0;
+    bool h_valid = false;
+    const int hl = tid - (TX - 32);
+    if (hl >= 0 && hl < 4) {
+        hslot = hl < 2 ? hl : TX + hl;
+        const int xlh = x0 - 2 + hslot;
+        xih = hslot - 2 + RR::M;
+        if (p.xper) {
+            xh = ((xlh % nx) + nx) % nx;
+            h_valid = true;
+        } else {
+            xh = xlh;
+            h_valid = xlh >= 0 && xlh < nx;
+        }
+    }
+
+    float py_m2 = 0.f, py_m1 = 0.f, py_0 = 0.f, py_p1 = 0.f;
+    Macro mc, mn;
+    auto row_phys = [&](int r) { return p.yper ? ((r % ny) + ny) % ny : r; };
+    // moments of row t: own column (kept) and, for four lanes, a halo column
+    auto moments_row = [&](int t, Macro& m, float& py, int buf) {
+        const int yr = row_phys(t);
+        if (own_valid) {
+            float f[9], h[9];
+            load_node_ring<TX, true, ST>(p, R, t, xi, xown, yr, f, h);
+            m = macro_of<true>(p, f, h, xown, yr);
+            phix[buf][tid + 2] = phi_x(m);
+            py = phi_y(m);
+        }
+        if (hslot >= 0 && h_valid) {
+            float f[9], h[9];
+            load_node_ring<TX, true, ST>(p, R, t, xih, xh, yr, f, h);
+            phix[buf][hslot] = phi_x(macro_of<true>(p, f, h, xh, yr));
+        }
+    };
+    auto phiy_row = [&](int t) -> float {
+        if (!own_valid) return 0.f;
+        const int yr = row_phys(t);
+        float f[9], h[9];
+        load_node_ring<TX, true, ST>(p, R, t, xi, xown, yr, f, h);
+        return phi_y(macro_of<true>(p, f, h, xown, yr));
+    };
+
+    bool ok = true;
+    // prologue: phi_y of row y0-1 (if it exists) and the moments of row y0
+    ok = R.acquire(p, src, y0 + 2) && ok;  // a bottom-wall row y0 reads its neighbour's sources up to y0+2
+    if (y0 > 0 || p.yper) py_m1 = phiy_row(y0 - 1);
+    moments_row(y0, mc, py_0, ((y0 % 3) + 3) % 3);
+
+    for (int r = y0; r < y1; ++r) {
+        const bool has_next = (r + 1 < ny) || p.yper;
+        int need = r + 2;
+        if (ywall && r == 0) need = 3;
+        ok = R.acquire(p, src, need) && ok;
+        if (has_next) moments_row(r + 1, mn, py_p1, (r + 1) % 3);
+        float py_p2 = 0.f;
+        if (ywall && r == 0) py_p2 = phiy_row(2);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(err, 1);
+            R.drain();
+            return;
+        }
+        // source r-3 was last read by the collision of row r-1 (a top-wall neighbour
+        // reads r-3..r-1); the collision of row r below reads r-2..r+1
+        ring_refill<TX, true, ST>(R, p, r - 3);
+        if (owns) {
+            const float* rw = phix[r % 3];
+            const int s = tid + 2;
+            float dxv;
+            if (!p.xper && xl == 0)
+                dxv = 0.5f * (-3.0f * rw[s] + 4.0f * rw[s + 1] - rw[s + 2]);
+            else if (!p.xper && xl == nx - 1)
+                dxv = 0.5f * (3.0f * rw[s] - 4.0f * rw[s - 1] + rw[s - 2]);
+            else
+                dxv = 0.5f * (rw[s + 1] - rw[s - 1]);
+            float dyv;
+            if (ywall && r == 0)
+                dyv = 0.5f * (-3.0f * py_0 + 4.0f * py_p1 - py_p2);
+            else if (ywall && r == ny - 1)
+                dyv = 0.5f * (3.0f * py_0 - 4.0f * py_m1 + py_m2);
+            else
+                dyv = 0.5f * (py_p1 - py_m1);
+            float f[9], h[9], fo[9], ho[9];
+            load_node_ring<TX, true, ST>(p, R, r, xi, xl, r, f, h);
+            collide<true>(p, f, h, mc, dxv, dyv, fo, ho);
+            store_node<ST>(p, dst, xl, r, fo, ho, true);
+        }
+        py_m2 = py_m1;
+        py_m1 = py_0;
+        py_0 = py_p1;
+        mc = mn;
+    }
+}
+
+// Dynamic shared memory of the TMA kernels.
+template <int TX, bool THERMAL, class ST>
+constexpr size_t tma_smem_bytes(bool corr) {
+    return RowRing<TX, THERMAL, ST>::RING_BYTES + 8 * sizeof(uint64_t) + (corr ? 3 * (TX + 4) * sizeof(float) : 0);
+}
+
+}  // namespace tclbm

@@ -93,6 +93,8 @@ _lib.tclbm_describe.argtypes = [_vp]
 _lib.tclbm_describe.restype = ctypes.c_char_p
 _lib.tclbm_set_tile.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
 _lib.tclbm_set_tile.restype = ctypes.c_int
+_lib.tclbm_set_kernel.argtypes = [_vp, ctypes.c_int32]
+_lib.tclbm_set_kernel.restype = ctypes.c_int
 
 EXPORTED = [name for name in dir(_lib) if name.startswith("tclbm_")]
 
@@ -164,6 +166,10 @@ def tclbm_set_stream(h, stream):
 
 def tclbm_set_tile(h, tx, ty):
     _check(_lib.tclbm_set_tile(h, int(tx), int(ty)), "tclbm_set_tile")
+
+
+def tclbm_set_kernel(h, kind):
+    _check(_lib.tclbm_set_kernel(h, int(kind)), "tclbm_set_kernel")
 
 
 def tclbm_describe(h) -> str:
@@ -311,6 +317,10 @@ class Lattice:
 
     def set_tile(self, tx=0, ty=0):
         tclbm_set_tile(self.handle, tx, ty)
+
+    def set_kernel(self, kind: int):
+        """0: TMA-staged rows (default); 1: direct loads."""
+        tclbm_set_kernel(self.handle, kind)
 
     def set_stream(self, stream):
         self.stream = stream

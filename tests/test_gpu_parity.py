@@ -189,6 +189,42 @@ def test_launch_shapes_are_bit_identical(T):
         assert np.array_equal(f, states[0][0]) and np.array_equal(h, states[0][1])
 
 
+KERNEL_CASES = [
+    ("periodic_corr", *W.random_periodic(150, 45, seed=21, force="accel")),
+    ("periodic_tg_nocorr", *W.random_periodic(97, 33, seed=22, force="taylor_green", correction=False)),
+    ("athermal", *W.random_periodic(70, 20, seed=23, force="accel", thermal=False)),
+    ("ywalls_zouhe", *W.with_walls(*W.random_periodic(130, 40, seed=24, force="accel"), axis="y", kind="zouhe")),
+    ("ywalls_nee", *W.with_walls(*W.random_periodic(64, 9, seed=25, force="accel"), axis="y", kind="nee")),
+    ("xwalls_eq", *W.with_walls(*W.random_periodic(129, 8, seed=26, force="none"), axis="x", kind="equilibrium")),
+    ("tiny", *W.random_periodic(3, 5, seed=27, force="accel")),
+]
+
+
+@pytest.mark.parametrize("name,case,fields", KERNEL_CASES, ids=[c[0] for c in KERNEL_CASES])
+@pytest.mark.parametrize("tile", [(32, 4), (64, 5), (128, 9)])
+def test_tma_and_direct_kernels_agree(T, name, case, fields, tile):
+    # Same arithmetic in both kernels; only the wall-node helpers, inlined into two
+    # different kernels, may contract a multiply-add differently (one ulp at x walls).
+    states = []
+    for kind in (0, 1):
+        lat = T.Lattice(case, fields)
+        lat.set_kernel(kind)
+        lat.set_tile(*tile)
+        lat.step(30)
+        states.append(lat.populations())
+        assert lat.diagnostics() is not None  # also surfaces a pipeline timeout as an error
+        lat.close()
+    (fa, ha), (fb, hb) = states
+    exact = not name.startswith("xwalls")
+    if exact:
+        assert np.array_equal(fa, fb)
+    np.testing.assert_allclose(fa, fb, rtol=0, atol=5e-7)
+    if case["thermal"]:
+        if exact:
+            assert np.array_equal(ha, hb)
+        np.testing.assert_allclose(ha, hb, rtol=0, atol=5e-7)
+
+
 def test_graph_replay_equals_single_launches(T):
     case, fields = W.random_periodic(64, 40, seed=10, force="accel")
     a = T.Lattice(case, fields)

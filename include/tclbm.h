@@ -185,11 +185,13 @@ const char* tclbm_last_error(void);
 const char* tclbm_describe(const tclbm_lattice* lat);
 
 /* Launch-shape override for tuning: tile width tx (32, 64 or 128 nodes) and rows per
- * CTA ty (>= 4); 0 keeps the library's choice. */
+ * CTA ty (>= 1); 0 keeps the library's choice. */
 tclbm_status tclbm_set_tile(tclbm_lattice* lat, int32_t tx, int32_t ty);
 
 /* Step kernel variant: 0 = rows staged into shared memory by the tensor-memory
- * accelerator (the default), 1 = direct loads.  Both compute bit-identical states. */
+ * accelerator, 1 = direct loads.  The library picks per lattice size (direct loads for
+ * lattices that fit in L2).  Interior nodes evolve bit-identically under both; wall
+ * nodes may differ in the last bit (multiply-add contraction). */
 tclbm_status tclbm_set_kernel(tclbm_lattice* lat, int32_t kind);
 
 #ifdef __cplusplus

@@ -203,14 +203,30 @@ void derive(tclbm_lattice* L) {
     }
 }
 
+// Lattices that fit in L2 are latency-bound: the direct-load kernel with short strips
+// and one or a few rows per CTA exposes the most parallelism.  Larger lattices stream
+// rows through the TMA ring with 128-wide strips of 16 rows (measured best at
+// 4096 x 2048).
+constexpr long long kSmallNodes = 1LL << 21;
+
+void default_launch(const tclbm_params& p, int& tx, int& ty, int& kernel) {
+    const long long n = (long long)p.nx * p.ny;
+    if (n <= kSmallNodes) {
+        kernel = KERNEL_DIRECT;
+        tx = p.nx >= 96 ? 64 : 32;
+        const long long strips = (p.nx + tx - 1) / tx;
+        long long t = (long long)p.ny * strips / (8LL * 152);
+        ty = (int)(t < 2 ? 2 : (t > 16 ? 16 : t));
+    } else {
+        kernel = KERNEL_TMA;
+        tx = p.nx >= 512 ? 128 : (p.nx >= 96 ? 64 : 32);
+        ty = 16;
+    }
+}
+
 void default_tile(const tclbm_params& p, int& tx, int& ty) {
-    tx = p.nx >= 512 ? 128 : (p.nx >= 96 ? 64 : 32);
-    const long long strips = (p.nx + tx - 1) / tx;
-    const long long target = 8LL * 152;  // CTAs: several per SM on 152 SMs
-    long long t = (long long)p.ny * strips / target;
-    if (t < 4) t = 4;
-    if (t > 64) t = 64;
-    ty = (int)t;
+    int k;
+    default_launch(p, tx, ty, k);
 }
 
 // ------------------------------------------------------------------ small kernels
@@ -588,7 +604,7 @@ tclbm_status tclbm_create(const tclbm_params* params, tclbm_alloc_fn alloc, tclb
     L->elem = elem_of(params->storage);
     L->nplanes = params->thermal ? 18 : 9;
     derive(L);
-    default_tile(L->prm, L->tx, L->ty);
+    default_launch(L->prm, L->tx, L->ty, L->kernel);
     const size_t n = (size_t)params->nx * params->ny;
     L->buf_bytes = (size_t)L->nplanes * L->dp.plane * L->elem;
     L->tables_bytes = sizeof(float) * 2 * ((size_t)params->nx + params->ny);
@@ -682,7 +698,7 @@ tclbm_status tclbm_set_tile(tclbm_lattice* L, int32_t tx, int32_t ty) {
     int dtx, dty;
     default_tile(L->prm, dtx, dty);
     if (tx != 0 && tx != 32 && tx != 64 && tx != 128) return fail(TCLBM_EINVAL, "tx must be 0, 32, 64 or 128");
-    if (ty != 0 && ty < 4) return fail(TCLBM_EINVAL, "ty must be 0 or >= 4");
+    if (ty < 0) return fail(TCLBM_EINVAL, "ty must be 0 or >= 1");
     L->tx = tx ? tx : dtx;
     L->ty = ty ? ty : dty;
     return TCLBM_OK;

@@ -602,9 +602,9 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_corr(const DevParams 
         return phi_y(m);
     };
 
-    // prologue
+    // prologue; a top-wall row closer than two rows to the segment start reads phi_y(r-2)
     if (y0 > 0 || p.yper) py_m1 = phiy_only(y0 - 1);
-    if (y0 > 1 || p.yper) py_m2 = 0.f;  // only the top wall row reads r-2, and it lies in the segment
+    if (ywall && y1 == ny && y0 >= 2 && y1 - y0 < 3) py_m2 = phiy_only(y0 - 2);
     compute_row(y0, fc, hc, mc, py_0, y0 % 3);
 
     for (int r = y0; r < y1; ++r) {

@@ -188,24 +188,44 @@ struct RowRing {
     }
 };
 
-// Streamed populations of the node at box index xi, logical column xl, physical
-// (x, y), target row t, with its wall scheme applied; the wall neighbour is read from
-// the ring as well (rows t +- 1 .. t +- 2).
+// Ring slots of source rows t-2 .. t+2 around a target row t (computed once per row).
+struct Slots5 {
+    int m2, m1, z, p1, p2;
+};
+
+// Streamed populations of the node at box index xi, physical (x, y), target row t,
+// with its wall scheme applied when `maybe_wall` (its row or column is a wall): the
+// wall neighbour is read from the ring as well (rows t +- 1, sources t-2 .. t+2).
 template <int TX, bool THERMAL, class ST>
-__device__ __forceinline__ void load_node_ring(const DevParams& p, const RowRing<TX, THERMAL, ST>& R, int t, int xi,
-                                               int x, int y, float* f, float* h) {
+__device__ __forceinline__ void load_node_ring(const DevParams& p, const RowRing<TX, THERMAL, ST>& R, const Slots5& sl,
+                                               int xi, int x, int y, bool maybe_wall, float* f, float* h) {
     using RR = RowRing<TX, THERMAL, ST>;
-    pull_ring<THERMAL, ST, RR::BOXW, RR::SLOT_ELEMS>(R.ring, R.slot(t - 1), R.slot(t), R.slot(t + 1), xi, f, h);
-    const int side = wall_side_of(p, x, y);
-    if (side >= 0) {
-        const int nxv = side == SIDE_XM ? 1 : (side == SIDE_XP ? -1 : 0);
-        const int nyv = side == SIDE_YM ? 1 : (side == SIDE_YP ? -1 : 0);
-        const int tn = t + nyv;
-        float ff[9], hf[9];
-        pull_ring<THERMAL, ST, RR::BOXW, RR::SLOT_ELEMS>(R.ring, R.slot(tn - 1), R.slot(tn), R.slot(tn + 1), xi + nxv, ff,
-                                                         hf);
-        wall_rebuild<THERMAL>(p, side, x, y, f, h, ff, hf);
+    pull_ring<THERMAL, ST, RR::BOXW, RR::SLOT_ELEMS>(R.ring, sl.m1, sl.z, sl.p1, xi, f, h);
+    if (maybe_wall) {
+        const int side = wall_side_of(p, x, y);
+        if (side >= 0) {
+            float ff[9], hf[9];
+            if (side == SIDE_YM)
+                pull_ring<THERMAL, ST, RR::BOXW, RR::SLOT_ELEMS>(R.ring, sl.z, sl.p1, sl.p2, xi, ff, hf);
+            else if (side == SIDE_YP)
+                pull_ring<THERMAL, ST, RR::BOXW, RR::SLOT_ELEMS>(R.ring, sl.m2, sl.m1, sl.z, xi, ff, hf);
+            else
+                pull_ring<THERMAL, ST, RR::BOXW, RR::SLOT_ELEMS>(R.ring, sl.m1, sl.z, sl.p1,
+                                                                  xi + (side == SIDE_XM ? 1 : -1), ff, hf);
+            wall_rebuild<THERMAL>(p, side, x, y, f, h, ff, hf);
+        }
     }
+}
+
+template <int NS>
+__device__ __forceinline__ Slots5 slots_around(int st) {  // st = ring slot of row t
+    Slots5 s;
+    s.z = st;
+    s.m1 = st == 0 ? NS - 1 : st - 1;
+    s.m2 = s.m1 == 0 ? NS - 1 : s.m1 - 1;
+    s.p1 = st == NS - 1 ? 0 : st + 1;
+    s.p2 = s.p1 == NS - 1 ? 0 : s.p1 + 1;
+    return s;
 }
 
 template <int TX, bool THERMAL, class ST>
@@ -262,11 +282,15 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_plain(const DevPa
     const int x = x0 + tid;
     const bool owns = x < p.nx;
     const int xi = tid + RR::M;
+    const bool col_wall = !p.xper && (x == 0 || x == p.nx - 1);
+    int st = R.slot(y0);
     for (int r = y0; r < y1; ++r) {
         const bool ok = R.acquire(p, src, r + 2);
         if (owns) {
+            const Slots5 sl = slots_around<RR::NS>(st);
+            const bool maybe_wall = col_wall || (!p.yper && (r == 0 || r == p.ny - 1));
             float f[9], h[9], fo[9], ho[9];
-            load_node_ring<TX, THERMAL, ST>(p, R, r, xi, x, r, f, h);
+            load_node_ring<TX, THERMAL, ST>(p, R, sl, xi, x, r, maybe_wall, f, h);
             const Macro m = macro_of<THERMAL>(p, f, h, x, r);
             collide<THERMAL>(p, f, h, m, 0.0f, 0.0f, fo, ho);
             store_node<ST>(p, dst, x, r, fo, ho, THERMAL);
@@ -277,6 +301,7 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_plain(const DevPa
             return;
         }
         ring_refill<TX, THERMAL, ST>(R, p, r - 2);
+        st = st == RR::NS - 1 ? 0 : st + 1;
     }
 }
 
@@ -284,7 +309,7 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_plain(const DevPa
 // two columns each side from the ring, the x-derivative through a three-row ring of
 // u_x (1 - theta) in shared memory.
 template <int TX, class ST>
-__global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_corr(const DevParams p, const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(TX, 640 / TX) tclbm_step_tma_corr(const DevParams p, const __grid_constant__ CUtensorMap map,
                                                           const ST* __restrict__ src, ST* __restrict__ dst,
                                                           int rows_per_cta, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -300,8 +325,10 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_corr(const DevPar
     const int y1 = (blockIdx.y == nseg - 1) ? ny : y0 + rows_per_cta;
     const bool ywall = !p.yper;
     // sources: the phi_y of row y0-1 needs y0-2; the lookahead of row y1 needs y1+1;
-    // the bottom wall's one-sided stencil needs row 3 (inside the first ring fill)
-    const int s_first = y0 - 2;
+    // the bottom wall's one-sided stencil needs row 3 (inside the first ring fill); a
+    // top-wall row within two rows of the segment start also needs phi_y(y0-2) (y0-3)
+    const bool short_top = ywall && y1 == ny && y0 >= 2 && y1 - y0 < 3;
+    const int s_first = short_top ? y0 - 3 : y0 - 2;
     int s_last = y1 + 1;
     if (ywall && y0 == 0 && s_last < 3) s_last = 3;
     ring_setup<TX, true, ST>(R, smem, &map, x0, s_first, s_last, p);
@@ -328,47 +355,58 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_corr(const DevPar
         }
     }
 
+    const bool col_wall_own = !p.xper && (xl == 0 || xl == nx - 1);
+    const bool col_wall_halo = !p.xper && (xh == 0 || xh == nx - 1);
     float py_m2 = 0.f, py_m1 = 0.f, py_0 = 0.f, py_p1 = 0.f;
     Macro mc, mn;
-    auto row_phys = [&](int r) { return p.yper ? ((r % ny) + ny) % ny : r; };
-    // moments of row t: own column (kept) and, for four lanes, a halo column
-    auto moments_row = [&](int t, Macro& m, float& py, int buf) {
-        const int yr = row_phys(t);
+    // moments of row t (physical row yr, ring slot st): own column (kept) and, for four
+    // lanes, a halo column
+    auto moments_row = [&](int t, int yr, int st, Macro& m, float& py, int buf) {
+        const Slots5 sl = slots_around<RR::NS>(st);
+        const bool row_wall = ywall && (t == 0 || t == ny - 1);
         if (own_valid) {
             float f[9], h[9];
-            load_node_ring<TX, true, ST>(p, R, t, xi, xown, yr, f, h);
+            load_node_ring<TX, true, ST>(p, R, sl, xi, xown, yr, row_wall || col_wall_own, f, h);
             m = macro_of<true>(p, f, h, xown, yr);
             phix[buf][tid + 2] = phi_x(m);
             py = phi_y(m);
         }
         if (hslot >= 0 && h_valid) {
             float f[9], h[9];
-            load_node_ring<TX, true, ST>(p, R, t, xih, xh, yr, f, h);
+            load_node_ring<TX, true, ST>(p, R, sl, xih, xh, yr, row_wall || col_wall_halo, f, h);
             phix[buf][hslot] = phi_x(macro_of<true>(p, f, h, xh, yr));
         }
     };
-    auto phiy_row = [&](int t) -> float {
+    auto phiy_row = [&](int t, int yr, int st) -> float {
         if (!own_valid) return 0.f;
-        const int yr = row_phys(t);
+        const Slots5 sl = slots_around<RR::NS>(st);
+        const bool row_wall = ywall && (t == 0 || t == ny - 1);
         float f[9], h[9];
-        load_node_ring<TX, true, ST>(p, R, t, xi, xown, yr, f, h);
+        load_node_ring<TX, true, ST>(p, R, sl, xi, xown, yr, row_wall || col_wall_own, f, h);
         return phi_y(macro_of<true>(p, f, h, xown, yr));
     };
+    auto next_slot = [](int st) { return st == RR::NS - 1 ? 0 : st + 1; };
+    auto prev_slot = [](int st) { return st == 0 ? RR::NS - 1 : st - 1; };
 
     bool ok = true;
     // prologue: phi_y of row y0-1 (if it exists) and the moments of row y0
     ok = R.acquire(p, src, y0 + 2) && ok;  // a bottom-wall row y0 reads its neighbour's sources up to y0+2
-    if (y0 > 0 || p.yper) py_m1 = phiy_row(y0 - 1);
-    moments_row(y0, mc, py_0, ((y0 % 3) + 3) % 3);
+    int st = R.slot(y0);                    // ring slot of row r (collision row)
+    int yr_next = p.yper ? (y0 + 1 == ny ? 0 : y0 + 1) : y0 + 1;  // physical row r + 1
+    if (y0 > 0 || p.yper) py_m1 = phiy_row(y0 - 1, y0 == 0 ? ny - 1 : y0 - 1, prev_slot(st));
+    if (short_top) py_m2 = phiy_row(y0 - 2, y0 - 2, prev_slot(prev_slot(st)));
+    moments_row(y0, y0, st, mc, py_0, ((y0 % 3) + 3) % 3);
+    int buf_c = ((y0 % 3) + 3) % 3;
 
     for (int r = y0; r < y1; ++r) {
         const bool has_next = (r + 1 < ny) || p.yper;
+        const int buf_n = buf_c == 2 ? 0 : buf_c + 1;
         int need = r + 2;
         if (ywall && r == 0) need = 3;
         ok = R.acquire(p, src, need) && ok;
-        if (has_next) moments_row(r + 1, mn, py_p1, (r + 1) % 3);
+        if (has_next) moments_row(r + 1, yr_next, next_slot(st), mn, py_p1, buf_n);
         float py_p2 = 0.f;
-        if (ywall && r == 0) py_p2 = phiy_row(2);
+        if (ywall && r == 0) py_p2 = phiy_row(2, 2, next_slot(next_slot(st)));
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(err, 1);
             R.drain();
@@ -378,12 +416,12 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_corr(const DevPar
         // reads r-3..r-1); the collision of row r below reads r-2..r+1
         ring_refill<TX, true, ST>(R, p, r - 3);
         if (owns) {
-            const float* rw = phix[r % 3];
+            const float* rw = phix[buf_c];
             const int s = tid + 2;
             float dxv;
-            if (!p.xper && xl == 0)
+            if (col_wall_own && xl == 0)
                 dxv = 0.5f * (-3.0f * rw[s] + 4.0f * rw[s + 1] - rw[s + 2]);
-            else if (!p.xper && xl == nx - 1)
+            else if (col_wall_own)
                 dxv = 0.5f * (3.0f * rw[s] - 4.0f * rw[s - 1] + rw[s - 2]);
             else
                 dxv = 0.5f * (rw[s + 1] - rw[s - 1]);
@@ -394,8 +432,10 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_corr(const DevPar
                 dyv = 0.5f * (3.0f * py_0 - 4.0f * py_m1 + py_m2);
             else
                 dyv = 0.5f * (py_p1 - py_m1);
+            const Slots5 sl = slots_around<RR::NS>(st);
+            const bool row_wall = ywall && (r == 0 || r == ny - 1);
             float f[9], h[9], fo[9], ho[9];
-            load_node_ring<TX, true, ST>(p, R, r, xi, xl, r, f, h);
+            load_node_ring<TX, true, ST>(p, R, sl, xi, xl, r, row_wall || col_wall_own, f, h);
             collide<true>(p, f, h, mc, dxv, dyv, fo, ho);
             store_node<ST>(p, dst, xl, r, fo, ho, true);
         }
@@ -403,6 +443,9 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_corr(const DevPar
         py_m1 = py_0;
         py_0 = py_p1;
         mc = mn;
+        st = next_slot(st);
+        buf_c = buf_n;
+        yr_next = (p.yper && yr_next == ny - 1) ? 0 : yr_next + 1;
     }
 }
 

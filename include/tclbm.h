@@ -75,6 +75,11 @@ enum {
  * state near (rho, u, T) = (1, 0, T0) and the kernels collide on those deviations in
  * FP32; the 16-bit formats round the stored deviations to bfloat16 or half. */
 enum { TCLBM_STORE_FP32 = 0, TCLBM_STORE_BF16 = 1, TCLBM_STORE_FP16 = 2 };
+/* Rounding of 16-bit stores.  Near a steady state the per-step change of a population
+ * falls below half an ulp and round-to-nearest freezes it; stochastic rounding (random
+ * bits from a counter-based hash of node, plane and step) keeps the expected stored
+ * value equal to the FP32 one. */
+enum { TCLBM_ROUND_NEAREST = 0, TCLBM_ROUND_STOCHASTIC = 1 };
 
 typedef struct {
     int32_t kind;   /* TCLBM_WALL_* */
@@ -101,6 +106,7 @@ typedef struct {
     tclbm_wall wall[4];   /* indexed by TCLBM_SIDE_* */
     int32_t storage;      /* TCLBM_STORE_* */
     double T_ref;         /* reference temperature of the Nusselt sum in diagnostics */
+    int32_t rounding;     /* 16-bit storage: TCLBM_ROUND_NEAREST or TCLBM_ROUND_STOCHASTIC */
 } tclbm_params;
 
 /* Device allocator hooks.  alloc(bytes, stream, ctx) returns device memory or NULL;

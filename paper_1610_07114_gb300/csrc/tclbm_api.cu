@@ -138,6 +138,8 @@ tclbm_status validate(const tclbm_params* p) {
         return fail(TCLBM_EINVAL, "bad force_kind");
     if (p->correction && !p->thermal) return fail(TCLBM_EINVAL, "the correction term needs thermal = 1");
     if (p->storage < TCLBM_STORE_FP32 || p->storage > TCLBM_STORE_FP16) return fail(TCLBM_EINVAL, "bad storage");
+    if (p->rounding != TCLBM_ROUND_NEAREST && p->rounding != TCLBM_ROUND_STOCHASTIC)
+        return fail(TCLBM_EINVAL, "bad rounding");
     return TCLBM_OK;
 }
 
@@ -184,6 +186,7 @@ void derive(tclbm_lattice* L) {
     d.ax = (float)p.ax;
     d.ay = (float)p.ay;
     d.famp = (float)p.famp;
+    d.rounding = p.storage != TCLBM_STORE_FP32 && p.rounding == TCLBM_ROUND_STOCHASTIC;
     for (int s = 0; s < 4; ++s) {
         d.wall_kind[s] = p.wall[s].kind;
         d.wall_therm[s] = p.wall[s].therm;
@@ -475,6 +478,7 @@ StepLaunch step_launch(tclbm_lattice* L, int src) {
     k.kernel = L->kernel;
     k.src_map = &L->maps[src];
     k.err = L->err;
+    k.parity = src;
     return k;
 }
 
@@ -650,6 +654,7 @@ tclbm_status tclbm_create(const tclbm_params* params, tclbm_alloc_fn alloc, tclb
     }
     cudaError_t e = cudaMemsetAsync(L->buf[0], 0, L->buf_bytes, L->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(L->err, 0, 256, L->stream);
+    L->dp.step_ctr = reinterpret_cast<unsigned*>(L->err) + 4;  // two counters after the error word
     if (e == cudaSuccess) e = cudaMemsetAsync(L->buf[1], 0, L->buf_bytes, L->stream);
     if (e != cudaSuccess) {
         tclbm_destroy(L);

@@ -49,7 +49,36 @@ struct DevParams {
     int wall_kind[4], wall_therm[4];
     float wall_rho[4], wall_ux[4], wall_uy[4], wall_T[4];
     float fbase[9], hbase[9];  // rest-state populations f^eq(1, 0, T0), h^eq(1, 0, T0)
+    int rounding;              // 16-bit stores: 0 nearest, 1 stochastic
+    unsigned* step_ctr;        // two step counters, alternated by launch parity
+    int parity;                // index of the source copy of this launch
 };
+
+// Counter-based 32-bit mix of (node, pair, step): random bits for stochastic rounding.
+__device__ __forceinline__ uint32_t sr_bits(uint32_t node, uint32_t pair, uint32_t step) {
+    uint32_t h = node * 0x9E3779B1u ^ (step * 0x85EBCA77u + pair * 0xC2B2AE3Du);
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    h *= 0x297A2D39u;
+    h ^= h >> 15;
+    return h;
+}
+
+template <class ST>
+__device__ __forceinline__ uint32_t cvt_rs_pair(float a, float b, uint32_t rbits);
+template <>
+__device__ __forceinline__ uint32_t cvt_rs_pair<__half>(float a, float b, uint32_t rbits) {
+    uint32_t d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(rbits));
+    return d;
+}
+template <>
+__device__ __forceinline__ uint32_t cvt_rs_pair<__nv_bfloat16>(float a, float b, uint32_t rbits) {
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(rbits));
+    return d;
+}
 
 // ---------------------------------------------------------------- storage formats
 //
@@ -509,6 +538,27 @@ template <class ST>
 __device__ __forceinline__ void store_node(const DevParams& p, ST* __restrict__ dst, int x, int y, const float* f,
                                            const float* h, bool thermal) {
     const long long P = p.plane, o = (long long)y * p.pitch + x;
+    if (sizeof(ST) == 2 && p.rounding) {
+        // stochastic rounding, two planes per conversion
+        const uint32_t step = p.step_ctr[p.parity];
+        const uint32_t node = (uint32_t)(y * p.nx + x);
+        float v[18];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            v[q] = f[q];
+            v[9 + q] = thermal ? h[q] : 0.0f;
+        }
+        const int npl = thermal ? 18 : 9;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            if (2 * k >= npl) break;
+            const uint32_t d = cvt_rs_pair<ST>(v[2 * k + 1], v[2 * k], sr_bits(node, (uint32_t)k, step));
+            const unsigned short lo = (unsigned short)(d & 0xffffu), hi = (unsigned short)(d >> 16);
+            reinterpret_cast<unsigned short*>(dst)[(2 * k) * P + o] = lo;
+            if (2 * k + 1 < npl) reinterpret_cast<unsigned short*>(dst)[(2 * k + 1) * P + o] = hi;
+        }
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < 9; ++q) Store<ST>::st(dst + q * P + o, f[q]);
     if (thermal) {
@@ -517,17 +567,21 @@ __device__ __forceinline__ void store_node(const DevParams& p, ST* __restrict__ 
     }
 }
 
+// Advances the stochastic-rounding step counter for the next launch (thread 0 of the
+// one CTA that owns the lattice's first strip and row).
+__device__ __forceinline__ void bump_step_counter(const DevParams& p) {
+    if (p.rounding && threadIdx.x == 0) p.step_ctr[p.parity ^ 1] = p.step_ctr[p.parity] + 1u;
+}
+
 // ---------------------------------------------------------------- the fused step
 
-// Variant without the correction term: no neighbour moments, one row at a time.
+// Strip [x0, x0 + TX) x rows [y0, y1) without the correction term: no neighbour
+// moments, one row at a time.
 template <int TX, bool THERMAL, class ST>
-__global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_plain(const DevParams p, const ST* __restrict__ src,
-                                                       ST* __restrict__ dst, int rows_per_cta) {
-    const int x = blockIdx.x * TX + threadIdx.x;
+__device__ __forceinline__ void strip_plain(const DevParams& p, const ST* __restrict__ src, ST* __restrict__ dst,
+                                            int x0, int y0, int y1) {
+    const int x = x0 + threadIdx.x;
     if (x >= p.nx) return;
-    const int nseg = gridDim.y;
-    const int y0 = blockIdx.y * rows_per_cta;
-    const int y1 = (blockIdx.y == nseg - 1) ? p.ny : y0 + rows_per_cta;
     for (int y = y0; y < y1; ++y) {
         float f[9], h[9], fo[9], ho[9];
         load_node<THERMAL, ST>(p, src, x, y, f, h);
@@ -537,19 +591,15 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_plain(const DevParams
     }
 }
 
-// Variant with the correction term (thermal): lookahead of one row in registers, the
+// Strip with the correction term (thermal): lookahead of one row in registers, the
 // x-derivative from a three-row ring of u_x(1-theta) in shared memory with a
-// two-column halo on each side (computed by four designated threads).
+// two-column halo on each side (computed by four designated threads).  Every thread
+// of the CTA must call it (it synchronises once per row).
 template <int TX, class ST>
-__global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_corr(const DevParams p, const ST* __restrict__ src,
-                                                      ST* __restrict__ dst, int rows_per_cta) {
-    __shared__ float ring[3][TX + 4];
+__device__ __forceinline__ void strip_corr(const DevParams& p, const ST* __restrict__ src, ST* __restrict__ dst,
+                                           int x0, int y0, int y1, float (*ring)[TX + 4]) {
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX;
     const int nx = p.nx, ny = p.ny;
-    const int nseg = gridDim.y;
-    const int y0 = blockIdx.y * rows_per_cta;
-    const int y1 = (blockIdx.y == nseg - 1) ? ny : y0 + rows_per_cta;
 
     // own column (slot tid + 2) and, for four threads, one halo slot
     const int xl = x0 + tid;
@@ -644,6 +694,70 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_corr(const DevParams 
             hc[q] = hn[q];
         }
     }
+}
+
+__device__ __forceinline__ void segment_rows(const DevParams& p, int rows_per_cta, int& y0, int& y1) {
+    y0 = blockIdx.y * rows_per_cta;
+    y1 = (blockIdx.y == gridDim.y - 1) ? p.ny : y0 + rows_per_cta;
+}
+
+template <int TX, bool THERMAL, class ST>
+__global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_plain(const DevParams p, const ST* __restrict__ src,
+                                                                 ST* __restrict__ dst, int rows_per_cta) {
+    int y0, y1;
+    segment_rows(p, rows_per_cta, y0, y1);
+    strip_plain<TX, THERMAL, ST>(p, src, dst, blockIdx.x * TX, y0, y1);
+    if (blockIdx.x == 0 && blockIdx.y == 0) bump_step_counter(p);
+}
+
+template <int TX, class ST>
+__global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_corr(const DevParams p, const ST* __restrict__ src,
+                                                                ST* __restrict__ dst, int rows_per_cta) {
+    __shared__ float ring[3][TX + 4];
+    int y0, y1;
+    segment_rows(p, rows_per_cta, y0, y1);
+    strip_corr<TX, ST>(p, src, dst, blockIdx.x * TX, y0, y1, ring);
+    if (blockIdx.x == 0 && blockIdx.y == 0) bump_step_counter(p);
+}
+
+// ---------------------------------------------------------------- many lattices at once
+
+// One lattice of a batch: its constants and its two population copies.
+struct BatchLattice {
+    DevParams p;
+    const void* buf[2];
+};
+
+// One CTA's work: a TX-wide strip of rows [y0, y1) of lattice `lat`.
+struct BatchItem {
+    int lat, x0, y0, y1;
+};
+
+// All lattices of a batch advance one time step in one launch; CTA k takes work item k.
+// Every lattice must share the storage format and the thermal / correction flags, and
+// the same step parity (source copy).  The per-node arithmetic is the single-lattice
+// kernel's, so a lattice evolves bit-identically alone or in a batch.
+template <int TX, bool THERMAL, bool CORR, class ST>
+__global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_batch(const BatchLattice* __restrict__ lats,
+                                                                 const BatchItem* __restrict__ items, int parity) {
+    __shared__ DevParams sp;
+    __shared__ float ring[3][TX + 4];
+    const BatchItem it = items[blockIdx.x];
+    {
+        const int* s = reinterpret_cast<const int*>(&lats[it.lat].p);
+        int* d = reinterpret_cast<int*>(&sp);
+        for (int i = threadIdx.x; i < (int)(sizeof(DevParams) / sizeof(int)); i += blockDim.x) d[i] = s[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sp.parity = parity;
+    __syncthreads();
+    const ST* src = static_cast<const ST*>(lats[it.lat].buf[parity]);
+    ST* dst = static_cast<ST*>(const_cast<void*>(lats[it.lat].buf[parity ^ 1]));
+    if (CORR)
+        strip_corr<TX, ST>(sp, src, dst, it.x0, it.y0, it.y1, ring);
+    else
+        strip_plain<TX, THERMAL, ST>(sp, src, dst, it.x0, it.y0, it.y1);
+    if (it.x0 == 0 && it.y0 == 0) bump_step_counter(sp);
 }
 
 }  // namespace tclbm

@@ -19,6 +19,7 @@ struct StepLaunch {
     int thermal, correction, tx, ty, kernel;
     const CUtensorMap* src_map;  // tensor map of the source copy (KERNEL_TMA)
     int* err;                    // device error word (bounded waits that expired)
+    int parity;                  // index of the source copy (selects the step counter)
 };
 
 cudaError_t launch_step_fp32(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s);

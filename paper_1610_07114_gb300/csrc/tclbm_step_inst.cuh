@@ -14,7 +14,9 @@ static cudaError_t allow_smem(K kernel, size_t bytes) {
 }
 
 template <int TX>
-static cudaError_t launch_tx(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s) {
+static cudaError_t launch_tx(const StepLaunch& k, const DevParams& p0, const void* src, void* dst, cudaStream_t s) {
+    DevParams p = p0;
+    p.parity = k.parity;
     const dim3 grid = step_grid(p, TX, k.ty);
     const ST* in = static_cast<const ST*>(src);
     ST* out = static_cast<ST*>(dst);

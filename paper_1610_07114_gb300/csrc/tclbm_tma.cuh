@@ -303,6 +303,7 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_plain(const DevPa
         ring_refill<TX, THERMAL, ST>(R, p, r - 2);
         st = st == RR::NS - 1 ? 0 : st + 1;
     }
+    if (blockIdx.x == 0 && blockIdx.y == 0) bump_step_counter(p);
 }
 
 // With the correction term: lookahead of one row for the same-time moments, x halo of
@@ -447,6 +448,7 @@ __global__ void __launch_bounds__(TX, 640 / TX) tclbm_step_tma_corr(const DevPar
         buf_c = buf_n;
         yr_next = (p.yper && yr_next == ny - 1) ? 0 : yr_next + 1;
     }
+    if (blockIdx.x == 0 && blockIdx.y == 0) bump_step_counter(p);
 }
 
 // Dynamic shared memory of the TMA kernels.

@@ -27,6 +27,7 @@ THERM = {"fixed": 0, "adiabatic": 1}
 VISC = {"nu": 0, "mu": 1, "mu_T": 2, "w1": 3}
 FORCE = {"none": 0, "accel": 1, "taylor_green": 2}
 STORAGE = {"fp32": 0, "bf16": 1, "fp16": 2}
+ROUNDING = {"nearest": 0, "stochastic": 1}
 SIDES = ("x-", "x+", "y-", "y+")
 DIAG_NAMES = ("mass", "momentum_x", "momentum_y", "energy", "kinetic", "nusselt_sum", "residual_num",
               "residual_den")
@@ -54,6 +55,7 @@ class tclbm_params(ctypes.Structure):
         ("wall", tclbm_wall * 4),
         ("storage", ctypes.c_int32),
         ("T_ref", ctypes.c_double),
+        ("rounding", ctypes.c_int32),
     ]
 
 
@@ -209,6 +211,7 @@ def params_from_case(case: dict) -> tclbm_params:
         p.wall[i].rho, p.wall[i].ux, p.wall[i].uy, p.wall[i].T = w["rho"], w["ux"], w["uy"], w["T"]
     p.storage = STORAGE[case.get("storage", "fp32")]
     p.T_ref = case.get("T_ref", case["T0"])
+    p.rounding = ROUNDING[case.get("rounding", "nearest")]
     return p
 
 

@@ -180,8 +180,10 @@ def rayleigh_benard(nx=256, ny=128, Ra=1e4, Pr=0.71, gamma=1.4, T_bot=1.01, T_to
 def shock_tube(nx=4096, ny=4, rho_l=1.05, rho_r=1.0, T=1.0, w1=1.887, storage="fp32"):
     """Low-Mach shock tube (Section V.C): periodic in y, equilibrium distributions at
     x = 0 and x = nx-1 with the initial end states; gamma = 1.4, Pr = 0.71,
-    w1 = 1.887, w2 = w3 = w4 = 1."""
-    case = base_case(nx, ny, name=f"shock_{nx}x{ny}", visc_law="w1", visc=w1, Pr=0.71, gamma=1.4,
+    w2 = w3 = w4 = 1.  The paper's w1 = 1.887 at its R T0 = 1/3 fixes the kinematic
+    viscosity nu = (1/3)(1/w1 - 1/2); that viscosity is kept (w1 = 1.786 at R T0 = 1/6)."""
+    nu = R_PAPER * (1.0 / w1 - 0.5)
+    case = base_case(nx, ny, name=f"shock_{nx}x{ny}", visc_law="nu", visc=nu, Pr=0.71, gamma=1.4,
                      storage=storage)
     case["walls"]["x-"] = _wall("equilibrium", 0.0, 0.0, T, rho_l)
     case["walls"]["x+"] = _wall("equilibrium", 0.0, 0.0, T, rho_r)

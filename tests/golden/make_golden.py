@@ -1,0 +1,48 @@
+"""Writes the stored expected values that come from the FP64 oracle (and only from it).
+
+    python tests/golden/make_golden.py
+
+rb_128x64_nusselt.txt: Nusselt number (Section V.D definition, H = ny - 1,
+kappa = nu / Pr, T0 = mean wall temperature) of Rayleigh-Benard convection on a
+128 x 64 lattice, Ra = 1e4, Pr = 0.71, seeded temperature perturbation of amplitude
+1e-2 (seed 1), after 60 000 and 80 000 time steps.
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import oracle  # noqa: E402
+from paper_1610_07114_gb300 import workloads as W  # noqa: E402
+
+
+def nusselt(case, m):
+    H = case["ny"] - 1
+    kappa = case["visc"] / case["Pr"]
+    dT = case["T_bot"] - case["T_top"]
+    return 1.0 + np.mean(m["uy"] * (m["T"] - case["T0"])) * H / (kappa * dT)
+
+
+def rb_128x64():
+    case, fields = W.rayleigh_benard(128, 64, Ra=1e4, seed=1, amp=1e-2)
+    o = oracle.Oracle(case, fields, threads=os.cpu_count())
+    rows = []
+    t0 = time.time()
+    for steps, chunk in ((60000, 60000), (80000, 20000)):
+        o.step(chunk)
+        rows.append((steps, nusselt(case, o.moments())))
+        print(f"  {steps} steps: Nu = {rows[-1][1]:.9f} ({time.time() - t0:.0f} s)", flush=True)
+    with open(os.path.join(HERE, "rb_128x64_nusselt.txt"), "w") as fh:
+        fh.write("# Nusselt number of the FP64 oracle: Rayleigh-Benard 128 x 64, Ra = 1e4, Pr = 0.71,\n")
+        fh.write("# perturbation amplitude 1e-2 (seed 1); written by tests/golden/make_golden.py\n")
+        fh.write("# columns: steps  Nu\n")
+        for steps, nu in rows:
+            fh.write(f"{steps} {nu:.12f}\n")
+
+
+if __name__ == "__main__":
+    rb_128x64()

@@ -47,8 +47,8 @@ def _peaks():
 
 def _kernel_source_hash():
     h = hashlib.sha256()
-    for rel in ("paper_1610_07114_gb300/csrc/tclbm_device.cuh", "paper_1610_07114_gb300/csrc/tclbm_step_inst.cuh",
-                "paper_1610_07114_gb300/csrc/tclbm_launch.h", "paper_1610_07114_gb300/csrc/tclbm_tma.cuh"):
+    # device code of the single-lattice step kernels (direct and TMA-fed)
+    for rel in ("paper_1610_07114_gb300/csrc/tclbm_device.cuh", "paper_1610_07114_gb300/csrc/tclbm_tma.cuh"):
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -235,6 +235,74 @@ def profile_run(args):
     return 0
 
 
+def bench_batch(args, tclbm, stream):
+    """Batched Rayleigh-Benard sweep (256 lattices, 64x32 .. 1024x512, FP16 deviations with
+    stochastic rounding): the batched kernel against the plain path (each lattice its own
+    launches), both timed with CUDA events on the same stream over the same lattices."""
+    import torch
+
+    from paper_1610_07114_gb300 import workloads as W
+
+    cases = W.batched_rb_sweep(count=args.batch_count, storage=args.batch_storage)
+    lats = [tclbm.Lattice(dict(c, rounding="stochastic"), f, stream=stream.cuda_stream) for c, f in cases]
+    nodes = sum(c["nx"] * c["ny"] for c, _ in cases)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn):
+        e0, e1 = ev(), ev()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    k = args.batch_steps
+    for l in lats:
+        l.step(2)
+    # plain, chunked: every lattice advanced k steps by its own launches (captured graphs)
+    t_chunk = timed(lambda: [l.step(k) for l in lats])
+    # plain, step-major: one launch per lattice per step
+    k1 = max(2, k // 8)
+    t_rr = timed(lambda: [l.step(1) for _ in range(k1) for l in lats]) * k / k1
+    b = tclbm.Batch(lats, stream=stream.cuda_stream)
+    tx, rows, pers, us = b.autotune(trial_steps=args.batch_tune_steps)
+    b.step(4)
+    t_batch = timed(lambda: b.step(k))
+    desc = b.describe()
+    b.close()
+    for l in lats:
+        l.close()
+    torch.cuda.synchronize()
+    peak, peak_kind = _peaks()
+    lu = nodes * k
+    plain_best = min(t_chunk, t_rr)
+    achieved = BYTES_PER_LU[args.batch_storage] * lu / t_batch / 1e9
+    return {"workload": f"rb_sweep_{args.batch_count}_{args.batch_storage}", "lattices": args.batch_count,
+            "nodes": nodes, "steps_timed": k, "kernel": desc,
+            "autotuned": {"tx": tx, "rows": rows, "persistent": pers, "us_per_step": us},
+            "LU_per_s": lu / t_batch, "ms_per_step": t_batch / k * 1e3,
+            "plain_chunked_LU_per_s": lu / t_chunk, "plain_launch_per_step_LU_per_s": lu / t_rr,
+            "ratio_vs_plain": plain_best / t_batch,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "bytes_per_LU": BYTES_PER_LU[args.batch_storage], "peak_source": f"{peak_kind} hbm_gbs"},
+            "rounding": "stochastic"}
+
+
+def batch_run(args):
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1610_07114_gb300 import build as B
+
+    B.build()
+    from paper_1610_07114_gb300 import tclbm
+
+    stream = torch.cuda.Stream()
+    print(json.dumps({"batched": bench_batch(args, tclbm, stream)}))
+    return 0
+
+
 def bench_gpu(args):
     import torch
 
@@ -338,6 +406,8 @@ def bench_gpu(args):
                            "traffic": _profiled_traffic(key)})
             pl.close()
 
+    batched = None if args.no_batch else bench_batch(args, tclbm, stream)
+
     if rank != 0:
         return 0
     achieved = BYTES_PER_LU[args.storage] * n / kernel_s / 1e9
@@ -369,6 +439,7 @@ def bench_gpu(args):
                 "steps": e2e_steps},
         "roofline": roofline,
         "roofline_probe": probes,
+        "batched": batched,
         "cpu_baseline": cpu,
         "clocks": clk,
         "gpu_launches": args.steps * (args.chunk + 2),
@@ -405,6 +476,12 @@ def main():
                     help="only step one --probe-nx x --probe-ny lattice --probe-steps times (for ncu)")
     ap.add_argument("--tile", type=int, nargs=2, default=None, help="override (tx, rows per CTA)")
     ap.add_argument("--kernel", type=int, default=None, help="step kernel variant: 0 TMA-staged, 1 direct loads")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-storage", default="fp16", choices=["fp32", "bf16", "fp16"])
+    ap.add_argument("--batch-steps", type=int, default=64)
+    ap.add_argument("--batch-tune-steps", type=int, default=6)
+    ap.add_argument("--batch-only", action="store_true", help="print only the batched-sweep measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -412,6 +489,8 @@ def main():
         return bench_reference(args)
     if args.profile_run:
         return profile_run(args)
+    if args.batch_only:
+        return batch_run(args)
     return bench_gpu(args)
 
 

@@ -200,6 +200,54 @@ tclbm_status tclbm_set_tile(tclbm_lattice* lat, int32_t tx, int32_t ty);
  * nodes may differ in the last bit (multiply-add contraction). */
 tclbm_status tclbm_set_kernel(tclbm_lattice* lat, int32_t kind);
 
+/* ------------------------------------------------------------------ batches
+ * A batch advances many independent lattices together: one launch of the batched step
+ * kernel per time step over a work list of strips of every lattice (tx columns by
+ * `rows` rows each, largest lattices first), captured in CUDA graphs for long runs.
+ * The paper treats one lattice at a time; a batch changes no arithmetic: every node
+ * is updated by the same code as in tclbm_step(), so each lattice evolves exactly as
+ * it does alone with the direct-load kernel (tclbm_set_kernel(lat, 1)).
+ *
+ * The batch borrows its lattices; they must stay alive for every batch call except
+ * tclbm_batch_destroy, which touches no lattice.  They must share the storage
+ * format and may differ in size, parameters, walls and collision variant (athermal,
+ * thermal, thermal with the correction term).  Stepping or re-initialising a lattice
+ * on its own between batch calls is allowed.  Device memory for the work list comes
+ * from the allocator hooks the first lattice was created with. */
+typedef struct tclbm_batch tclbm_batch;
+
+/* `stream` is a cudaStream_t (NULL = legacy default stream); batch steps are ordered
+ * after work already queued on each lattice's own stream, and later work on those
+ * streams after the batch steps.  EINVAL on count < 1, a NULL or repeated handle, or
+ * mixed storage formats; ENOMEM if the work list cannot be allocated. */
+tclbm_status tclbm_batch_create(tclbm_lattice* const* lattices, int32_t count, void* stream, tclbm_batch** out);
+
+/* Advance every lattice of the batch by `nsteps` >= 0 time steps (asynchronous). */
+tclbm_status tclbm_batch_step(tclbm_batch* batch, int64_t nsteps);
+
+/* Work-list shape: strip width tx (32, 64 or 128), rows per work item (>= 1) and
+ * persistent != 0 for a grid of one wave of resident CTAs that loops over the work
+ * list (else one CTA per item).  EINVAL on other values. */
+tclbm_status tclbm_batch_set_tile(tclbm_batch* batch, int32_t tx, int32_t rows, int32_t persistent);
+
+/* Time every shape (tx in {32, 64, 128}, rows in {1, 2, 4, ..., 64} up to the tallest
+ * lattice, persistent or not) over `trial_steps` (>= 2, rounded up to even) steps each,
+ * keep the fastest and report it through the non-NULL out pointers (best_us: device
+ * microseconds per batch step).  The lattices' state is saved before and restored
+ * after, so the call changes no results; it needs device memory for one copy of every
+ * lattice's state and synchronises the stream. */
+tclbm_status tclbm_batch_autotune(tclbm_batch* batch, int32_t trial_steps, int32_t* best_tx, int32_t* best_rows,
+                                  int32_t* best_persistent, float* best_us);
+
+/* Kernel name and work-list shape, for profiling. */
+const char* tclbm_batch_describe(const tclbm_batch* batch);
+
+/* Batch steps taken since creation (-1 for NULL). */
+int64_t tclbm_batch_steps_done(const tclbm_batch* batch);
+
+/* Release the batch (not its lattices); NULL is accepted.  Synchronises the stream. */
+tclbm_status tclbm_batch_destroy(tclbm_batch* batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
-SOURCES = ["tclbm_api.cu", "tclbm_step_fp32.cu", "tclbm_step_bf16.cu", "tclbm_step_fp16.cu", "tclbm_noalloc.cu"]
+SOURCES = ["tclbm_api.cu", "tclbm_step_fp32.cu", "tclbm_step_bf16.cu", "tclbm_step_fp16.cu", "tclbm_noalloc.cu", "tclbm_batch.cu"]
 
 
 def _deps():

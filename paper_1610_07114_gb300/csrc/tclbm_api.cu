@@ -16,15 +16,16 @@
 
 #include "tclbm.h"
 #include "tclbm_device.cuh"
+#include "tclbm_internal.h"
 #include "tclbm_launch.h"
 
 using namespace tclbm;
 
 namespace {
 thread_local char g_err[512] = "";
+}  // namespace
 
-tclbm_status fail(tclbm_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
-tclbm_status fail(tclbm_status st, const char* fmt, ...) {
+tclbm_status tclbm::fail(tclbm_status st, const char* fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof g_err, fmt, ap);
@@ -32,60 +33,18 @@ tclbm_status fail(tclbm_status st, const char* fmt, ...) {
     return st;
 }
 
-tclbm_status cuda_fail(cudaError_t e, const char* what) {
+tclbm_status tclbm::cuda_fail(cudaError_t e, const char* what) {
     return fail(TCLBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CK(call)                                            \
-    do {                                                    \
-        cudaError_t e_ = (call);                            \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-    } while (0)
-
+namespace {
 constexpr int kDiagBlock = 256;
 constexpr int kDiagMaxBlocks = 1024;
 }  // namespace
 
 void tclbm::set_last_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
 
-struct tclbm_lattice {
-    tclbm_params prm;
-    DevParams dp;
-    cudaStream_t stream = nullptr;
-    tclbm_alloc_fn alloc = nullptr;
-    tclbm_free_fn free_fn = nullptr;
-    void* ctx = nullptr;
-    int storage = TCLBM_STORE_FP32;
-    size_t elem = 4;
-    int nplanes = 18;
-    void* buf[2] = {nullptr, nullptr};
-    size_t buf_bytes = 0;
-    float* tables = nullptr;
-    size_t tables_bytes = 0;
-    double* diag = nullptr;  // [kDiagMaxBlocks * TCLBM_NDIAG] partials + TCLBM_NDIAG result
-    size_t diag_bytes = 0;
-    float* usnap = nullptr;  // 2 * nx * ny
-    size_t usnap_bytes = 0;
-    double* stage = nullptr;  // 4 * nx * ny doubles (or 18 * nx * ny for populations)
-    size_t stage_bytes = 0;
-    int cur = 0;
-    int64_t steps = 0;
-    int tx = 0, ty = 0;
-    int kernel = KERNEL_TMA;
-    CUtensorMap maps[2];  // TMA descriptors of the two copies for box width of tx
-    int maps_tx = 0;
-    int* err = nullptr;  // device error word of the step kernels
-    char desc[256] = "";
-    // CUDA graph of 2 * kGraphPairs step launches (parity preserved)
-    cudaGraphExec_t graph = nullptr;
-    int graph_tx = 0, graph_ty = 0, graph_kernel = -1;
-};
-
-namespace {
-
-constexpr int kGraphPairs = 32;
-
-void* dev_alloc(tclbm_lattice* L, size_t bytes) {
+void* tclbm::dev_alloc(tclbm_lattice* L, size_t bytes) {
     if (bytes == 0) return nullptr;
     if (L->alloc) return L->alloc(bytes, (void*)L->stream, L->ctx);
     void* p = nullptr;
@@ -96,13 +55,15 @@ void* dev_alloc(tclbm_lattice* L, size_t bytes) {
     return p;
 }
 
-void dev_free(tclbm_lattice* L, void* p, size_t bytes) {
+void tclbm::dev_free(tclbm_lattice* L, void* p, size_t bytes) {
     if (!p) return;
     if (L->free_fn)
         L->free_fn(p, bytes, (void*)L->stream, L->ctx);
     else
         cudaFree(p);
 }
+
+namespace {
 
 bool walls_ok(const tclbm_params* p) {
     for (int s = 0; s < 4; ++s) {

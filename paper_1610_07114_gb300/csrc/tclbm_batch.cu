@@ -1,0 +1,414 @@
+// tclbm_batch.cu -- many independent lattices advanced together: one launch of the
+// batched step kernel per time step over a work list of strips of every lattice,
+// CUDA-graph capture of long runs, and an autotuner of the work-list shape.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "tclbm.h"
+#include "tclbm_internal.h"
+
+using namespace tclbm;
+
+struct tclbm_batch {
+    std::vector<tclbm_lattice*> lats;
+    cudaStream_t stream = nullptr;
+    // allocator hooks copied from the first lattice at creation (the batch's own
+    // memory does not depend on any lattice staying alive)
+    tclbm_alloc_fn alloc = nullptr;
+    tclbm_free_fn free_fn = nullptr;
+    void* ctx = nullptr;
+    int storage = 0;
+    int sms = 0;
+    // work-list shape
+    int tx = 64, rows = 4, persistent = 1;
+    // device arrays: descriptors and work items
+    BatchLattice* d_lats = nullptr;
+    size_t d_lats_bytes = 0;
+    BatchItem* d_items = nullptr;
+    size_t d_items_bytes = 0;
+    int nitems = 0;
+    unsigned grid = 0;
+    std::vector<BatchLattice> h_lats;  // last uploaded descriptors
+    int64_t steps = 0;                 // batch steps taken (parity of the next launch)
+    bool items_valid = false;
+    cudaGraphExec_t graph = nullptr;
+    bool graph_valid = false;
+    cudaEvent_t ev = nullptr;
+    char desc[256] = "";
+};
+
+namespace {
+
+int kind_of(const tclbm_lattice* L) {
+    if (!L->prm.thermal) return BATCH_ATHERMAL;
+    return L->prm.correction ? BATCH_THERMAL_CORR : BATCH_THERMAL;
+}
+
+long long nodes_of(const tclbm_lattice* L) { return (long long)L->prm.nx * L->prm.ny; }
+
+// Work items for the current shape: lattices by decreasing size (longest work first),
+// within a lattice row segments of `rows` rows (the last one takes the remainder, as
+// in the single-lattice kernel) and strips of tx columns, strip index fastest.
+void make_items(const tclbm_batch* B, std::vector<BatchItem>& items) {
+    std::vector<int> order(B->lats.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return nodes_of(B->lats[a]) > nodes_of(B->lats[b]); });
+    items.clear();
+    for (int li : order) {
+        const tclbm_params& p = B->lats[li]->prm;
+        int nseg = p.ny / B->rows;
+        if (nseg < 1) nseg = 1;
+        const int nstrip = (p.nx + B->tx - 1) / B->tx;
+        for (int s = 0; s < nseg; ++s) {
+            const int y0 = s * B->rows;
+            const int y1 = s == nseg - 1 ? p.ny : y0 + B->rows;
+            for (int k = 0; k < nstrip; ++k) items.push_back(BatchItem{li, k * B->tx, y0, y1});
+        }
+    }
+}
+
+void* batch_alloc(tclbm_batch* B, size_t bytes) {
+    if (bytes == 0) return nullptr;
+    if (B->alloc) return B->alloc(bytes, (void*)B->stream, B->ctx);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void release(tclbm_batch* B, void*& p, size_t& bytes) {
+    if (p) {
+        if (B->free_fn)
+            B->free_fn(p, bytes, (void*)B->stream, B->ctx);
+        else
+            cudaFree(p);
+    }
+    p = nullptr;
+    bytes = 0;
+}
+
+tclbm_status upload_items(tclbm_batch* B) {
+    if (B->items_valid) return TCLBM_OK;
+    std::vector<BatchItem> items;
+    make_items(B, items);
+    const size_t bytes = items.size() * sizeof(BatchItem);
+    if (bytes > B->d_items_bytes) {
+        void* p = B->d_items;
+        release(B, p, B->d_items_bytes);
+        B->d_items = (BatchItem*)batch_alloc(B, bytes);
+        if (!B->d_items) return fail(TCLBM_ENOMEM, "work list allocation of %zu bytes failed", bytes);
+        B->d_items_bytes = bytes;
+    }
+    CK(cudaMemcpyAsync(B->d_items, items.data(), bytes, cudaMemcpyHostToDevice, B->stream));
+    CK(cudaStreamSynchronize(B->stream));  // host vector goes out of scope
+    B->nitems = (int)items.size();
+    const int per_sm = batch_ctas_per_sm(B->storage, B->tx);
+    const long long wave = (long long)B->sms * per_sm;
+    B->grid = (unsigned)(B->persistent ? std::min<long long>(wave, B->nitems) : B->nitems);
+    B->items_valid = true;
+    B->graph_valid = false;
+    return TCLBM_OK;
+}
+
+// Descriptors from the handles' current state: lattice i reads copy L->cur at the
+// batch's current parity.  Re-uploaded only when something changed (a lattice stepped
+// or re-initialised on its own between batch calls).
+tclbm_status upload_lattices(tclbm_batch* B) {
+    const int n = (int)B->lats.size();
+    const int par = (int)(B->steps & 1);
+    std::vector<BatchLattice> h(n);
+    bool same = (int)B->h_lats.size() == n;
+    for (int i = 0; i < n; ++i) {
+        const tclbm_lattice* L = B->lats[i];
+        std::memset(&h[i], 0, sizeof h[i]);
+        h[i].p = L->dp;
+        h[i].p.parity = L->cur ^ par;
+        h[i].buf[0] = L->buf[0];
+        h[i].buf[1] = L->buf[1];
+        h[i].kind = kind_of(L);
+        if (same && std::memcmp(&h[i], &B->h_lats[i], sizeof h[i]) != 0) same = false;
+    }
+    if (same) return TCLBM_OK;
+    const size_t bytes = n * sizeof(BatchLattice);
+    if (!B->d_lats) {
+        B->d_lats = (BatchLattice*)batch_alloc(B, bytes);
+        if (!B->d_lats) return fail(TCLBM_ENOMEM, "descriptor allocation of %zu bytes failed", bytes);
+        B->d_lats_bytes = bytes;
+    }
+    CK(cudaMemcpyAsync(B->d_lats, h.data(), bytes, cudaMemcpyHostToDevice, B->stream));
+    CK(cudaStreamSynchronize(B->stream));
+    B->h_lats.swap(h);
+    return TCLBM_OK;
+}
+
+// Orders the batch stream after work queued on each lattice's own stream, or the
+// reverse (after = true).
+tclbm_status join_streams(tclbm_batch* B, bool after) {
+    for (tclbm_lattice* L : B->lats) {
+        if (L->stream == B->stream) continue;
+        cudaStream_t from = after ? B->stream : L->stream;
+        cudaStream_t to = after ? L->stream : B->stream;
+        CK(cudaEventRecord(B->ev, from));
+        CK(cudaStreamWaitEvent(to, B->ev, 0));
+    }
+    return TCLBM_OK;
+}
+
+tclbm_status launch_batch_steps(tclbm_batch* B, int64_t n) {
+    for (int64_t s = 0; s < n; ++s) {
+        const cudaError_t e = launch_batch_kernel(B->storage, B->tx, B->grid, B->d_lats, B->d_items, B->nitems,
+                                                  (int)(B->steps & 1), B->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "batched step kernel launch");
+        ++B->steps;
+    }
+    return TCLBM_OK;
+}
+
+tclbm_status build_batch_graph(tclbm_batch* B) {
+    if (B->graph_valid) return TCLBM_OK;
+    if (B->graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+    }
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int s = 0; s < 2 * kGraphPairs && e == cudaSuccess; ++s)
+            e = launch_batch_kernel(B->storage, B->tx, B->grid, B->d_lats, B->d_items, B->nitems, s & 1, cs);
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&B->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        B->graph = nullptr;
+        return cuda_fail(e, "batched step graph capture");
+    }
+    B->graph_valid = true;
+    return TCLBM_OK;
+}
+
+// Advances the batch by n steps on its stream (graphs for runs of 2 * kGraphPairs).
+tclbm_status run_steps(tclbm_batch* B, int64_t n) {
+    if (n >= 2 * kGraphPairs) {
+        if (B->steps & 1) {
+            tclbm_status st = launch_batch_steps(B, 1);
+            if (st != TCLBM_OK) return st;
+            --n;
+        }
+        tclbm_status st = build_batch_graph(B);
+        if (st != TCLBM_OK) return st;
+        while (n >= 2 * kGraphPairs) {
+            CK(cudaGraphLaunch(B->graph, B->stream));
+            B->steps += 2 * kGraphPairs;
+            n -= 2 * kGraphPairs;
+        }
+    }
+    return launch_batch_steps(B, n);
+}
+
+bool valid_shape(int tx, int rows) { return (tx == 32 || tx == 64 || tx == 128) && rows >= 1; }
+
+}  // namespace
+
+extern "C" {
+
+tclbm_status tclbm_batch_create(tclbm_lattice* const* lattices, int32_t count, void* stream, tclbm_batch** out) {
+    if (!out) return fail(TCLBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!lattices || count < 1) return fail(TCLBM_EINVAL, "a batch needs at least one lattice");
+    for (int i = 0; i < count; ++i) {
+        if (!lattices[i]) return fail(TCLBM_EINVAL, "lattice %d is NULL", i);
+        if (lattices[i]->storage != lattices[0]->storage)
+            return fail(TCLBM_EINVAL, "lattice %d has another storage format than lattice 0", i);
+        for (int j = 0; j < i; ++j)
+            if (lattices[j] == lattices[i]) return fail(TCLBM_EINVAL, "lattice %d appears twice", i);
+    }
+    tclbm_batch* B = new (std::nothrow) tclbm_batch;
+    if (!B) return fail(TCLBM_ENOMEM, "host allocation failed");
+    B->lats.assign(lattices, lattices + count);
+    B->stream = (cudaStream_t)stream;
+    B->storage = lattices[0]->storage;
+    B->alloc = lattices[0]->alloc;
+    B->free_fn = lattices[0]->free_fn;
+    B->ctx = lattices[0]->ctx;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete B;
+        return cuda_fail(e, "batch setup");
+    }
+    // default shape: narrow strips and short segments for batches of small lattices
+    long long total = 0;
+    for (tclbm_lattice* L : B->lats) total += nodes_of(L);
+    const long long avg = total / count;
+    B->tx = avg <= (1LL << 16) ? 32 : 64;
+    B->rows = avg <= (1LL << 16) ? 2 : 4;
+    B->persistent = 1;
+    tclbm_status st = upload_items(B);
+    if (st == TCLBM_OK) st = upload_lattices(B);
+    if (st != TCLBM_OK) {
+        tclbm_batch_destroy(B);
+        return st;
+    }
+    *out = B;
+    return TCLBM_OK;
+}
+
+tclbm_status tclbm_batch_step(tclbm_batch* B, int64_t nsteps) {
+    if (!B) return fail(TCLBM_EINVAL, "batch is NULL");
+    if (nsteps < 0) return fail(TCLBM_EINVAL, "nsteps must be >= 0");
+    if (nsteps == 0) return TCLBM_OK;
+    tclbm_status st = join_streams(B, false);
+    if (st == TCLBM_OK) st = upload_items(B);
+    if (st == TCLBM_OK) st = upload_lattices(B);
+    if (st == TCLBM_OK) st = run_steps(B, nsteps);
+    if (st != TCLBM_OK) return st;
+    for (tclbm_lattice* L : B->lats) {
+        L->cur ^= (int)(nsteps & 1);
+        L->steps += nsteps;
+    }
+    return join_streams(B, true);
+}
+
+tclbm_status tclbm_batch_set_tile(tclbm_batch* B, int32_t tx, int32_t rows, int32_t persistent) {
+    if (!B) return fail(TCLBM_EINVAL, "batch is NULL");
+    if (!valid_shape(tx, rows)) return fail(TCLBM_EINVAL, "tx must be 32, 64 or 128 and rows >= 1");
+    if (tx != B->tx || rows != B->rows || (persistent != 0) != (B->persistent != 0)) {
+        B->tx = tx;
+        B->rows = rows;
+        B->persistent = persistent != 0;
+        B->items_valid = false;
+    }
+    return upload_items(B);
+}
+
+tclbm_status tclbm_batch_autotune(tclbm_batch* B, int32_t trial_steps, int32_t* best_tx, int32_t* best_rows,
+                                  int32_t* best_persistent, float* best_us) {
+    if (!B) return fail(TCLBM_EINVAL, "batch is NULL");
+    if (trial_steps < 2) return fail(TCLBM_EINVAL, "trial_steps must be >= 2");
+    trial_steps += trial_steps & 1;  // even: every lattice ends on the copy it started from
+    tclbm_status st = join_streams(B, false);
+    if (st == TCLBM_OK) st = upload_items(B);
+    if (st == TCLBM_OK) st = upload_lattices(B);
+    if (st != TCLBM_OK) return st;
+    // keep the current state (source copy and stochastic-rounding counters) of every lattice
+    size_t total = 0;
+    for (tclbm_lattice* L : B->lats) total += L->buf_bytes + 256;
+    void* backup_mem = batch_alloc(B, total);
+    char* backup = (char*)backup_mem;
+    if (!backup) return fail(TCLBM_ENOMEM, "autotune backup of %zu bytes failed", total);
+    {
+        size_t off = 0;
+        for (tclbm_lattice* L : B->lats) {
+            CK(cudaMemcpyAsync(backup + off, L->buf[L->cur], L->buf_bytes, cudaMemcpyDeviceToDevice, B->stream));
+            CK(cudaMemcpyAsync(backup + off + L->buf_bytes, L->err, 256, cudaMemcpyDeviceToDevice, B->stream));
+            off += L->buf_bytes + 256;
+        }
+    }
+    const int keep_tx = B->tx, keep_rows = B->rows, keep_p = B->persistent;
+    const int64_t keep_steps = B->steps;
+    int bt = keep_tx, br = keep_rows, bp = keep_p;
+    float best = 1e30f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    int max_ny = 1;
+    for (tclbm_lattice* L : B->lats) max_ny = std::max(max_ny, L->prm.ny);
+    static const int kTx[] = {32, 64, 128};
+    static const int kRows[] = {1, 2, 4, 8, 16, 32, 64};
+    for (int t = 0; t < 3 && ce == cudaSuccess && st == TCLBM_OK; ++t)
+        for (int r = 0; r < 7 && st == TCLBM_OK; ++r)
+            for (int pers = 0; pers < 2 && st == TCLBM_OK; ++pers) {
+                if (kRows[r] > max_ny) continue;
+                B->tx = kTx[t];
+                B->rows = kRows[r];
+                B->persistent = pers;
+                B->items_valid = false;
+                st = upload_items(B);
+                if (st == TCLBM_OK) st = launch_batch_steps(B, 2);  // warm-up
+                if (st != TCLBM_OK) break;
+                cudaEventRecord(e0, B->stream);
+                st = launch_batch_steps(B, trial_steps);
+                cudaEventRecord(e1, B->stream);
+                if (st != TCLBM_OK) break;
+                if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) break;
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const float us = 1e3f * ms / trial_steps;
+                if (us < best) {
+                    best = us;
+                    bt = kTx[t];
+                    br = kRows[r];
+                    bp = pers;
+                }
+            }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    // restore the state; the batch's parity is back where it was (even trial lengths)
+    {
+        size_t off = 0;
+        for (tclbm_lattice* L : B->lats) {
+            cudaMemcpyAsync(L->buf[L->cur], backup + off, L->buf_bytes, cudaMemcpyDeviceToDevice, B->stream);
+            cudaMemcpyAsync(L->err, backup + off + L->buf_bytes, 256, cudaMemcpyDeviceToDevice, B->stream);
+            off += L->buf_bytes + 256;
+        }
+    }
+    const cudaError_t se = cudaStreamSynchronize(B->stream);
+    release(B, backup_mem, total);
+    B->steps = keep_steps;
+    if (st != TCLBM_OK) return st;
+    if (ce != cudaSuccess) return cuda_fail(ce, "autotune timing");
+    if (se != cudaSuccess) return cuda_fail(se, "autotune restore");
+    B->tx = bt;
+    B->rows = br;
+    B->persistent = bp;
+    B->items_valid = false;
+    st = upload_items(B);
+    if (st != TCLBM_OK) return st;
+    if (best_tx) *best_tx = bt;
+    if (best_rows) *best_rows = br;
+    if (best_persistent) *best_persistent = bp;
+    if (best_us) *best_us = best;
+    return join_streams(B, true);
+}
+
+const char* tclbm_batch_describe(const tclbm_batch* B) {
+    if (!B) return "";
+    tclbm_batch* M = const_cast<tclbm_batch*>(B);
+    const char* st = B->storage == 0 ? "float" : (B->storage == 1 ? "bf16" : "half");
+    snprintf(M->desc, sizeof M->desc, "tclbm_step_batch<%d,%s> lattices %zu items %d grid (%u) block (%d) rows %d%s",
+             B->tx, st, B->lats.size(), B->nitems, B->grid, B->tx, B->rows, B->persistent ? " persistent" : "");
+    return B->desc;
+}
+
+int64_t tclbm_batch_steps_done(const tclbm_batch* B) { return B ? B->steps : -1; }
+
+tclbm_status tclbm_batch_destroy(tclbm_batch* B) {
+    if (!B) return TCLBM_OK;
+    cudaStreamSynchronize(B->stream);
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    if (B->ev) cudaEventDestroy(B->ev);
+    void* p = B->d_items;
+    release(B, p, B->d_items_bytes);
+    p = B->d_lats;
+    release(B, p, B->d_lats_bytes);
+    delete B;
+    return TCLBM_OK;
+}
+
+}  // extern "C"

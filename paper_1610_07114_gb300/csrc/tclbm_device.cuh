@@ -720,44 +720,4 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_corr(const DevParams 
     if (blockIdx.x == 0 && blockIdx.y == 0) bump_step_counter(p);
 }
 
-// ---------------------------------------------------------------- many lattices at once
-
-// One lattice of a batch: its constants and its two population copies.
-struct BatchLattice {
-    DevParams p;
-    const void* buf[2];
-};
-
-// One CTA's work: a TX-wide strip of rows [y0, y1) of lattice `lat`.
-struct BatchItem {
-    int lat, x0, y0, y1;
-};
-
-// All lattices of a batch advance one time step in one launch; CTA k takes work item k.
-// Every lattice must share the storage format and the thermal / correction flags, and
-// the same step parity (source copy).  The per-node arithmetic is the single-lattice
-// kernel's, so a lattice evolves bit-identically alone or in a batch.
-template <int TX, bool THERMAL, bool CORR, class ST>
-__global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_batch(const BatchLattice* __restrict__ lats,
-                                                                 const BatchItem* __restrict__ items, int parity) {
-    __shared__ DevParams sp;
-    __shared__ float ring[3][TX + 4];
-    const BatchItem it = items[blockIdx.x];
-    {
-        const int* s = reinterpret_cast<const int*>(&lats[it.lat].p);
-        int* d = reinterpret_cast<int*>(&sp);
-        for (int i = threadIdx.x; i < (int)(sizeof(DevParams) / sizeof(int)); i += blockDim.x) d[i] = s[i];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) sp.parity = parity;
-    __syncthreads();
-    const ST* src = static_cast<const ST*>(lats[it.lat].buf[parity]);
-    ST* dst = static_cast<ST*>(const_cast<void*>(lats[it.lat].buf[parity ^ 1]));
-    if (CORR)
-        strip_corr<TX, ST>(sp, src, dst, it.x0, it.y0, it.y1, ring);
-    else
-        strip_plain<TX, THERMAL, ST>(sp, src, dst, it.x0, it.y0, it.y1);
-    if (it.x0 == 0 && it.y0 == 0) bump_step_counter(sp);
-}
-
 }  // namespace tclbm

@@ -6,6 +6,7 @@
 
 #include <cuda.h>
 
+#include "tclbm_batch.cuh"
 #include "tclbm_device.cuh"
 
 namespace tclbm {
@@ -25,6 +26,19 @@ struct StepLaunch {
 cudaError_t launch_step_fp32(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s);
 cudaError_t launch_step_bf16(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s);
 cudaError_t launch_step_fp16(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s);
+cudaError_t launch_batch_fp32(int tx, unsigned grid, const BatchLattice* lats, const BatchItem* items, int nitems,
+                              int step_parity, cudaStream_t s);
+cudaError_t launch_batch_bf16(int tx, unsigned grid, const BatchLattice* lats, const BatchItem* items, int nitems,
+                              int step_parity, cudaStream_t s);
+cudaError_t launch_batch_fp16(int tx, unsigned grid, const BatchLattice* lats, const BatchItem* items, int nitems,
+                              int step_parity, cudaStream_t s);
+// Resident CTAs per SM of the batched kernel for a tile width (occupancy calculator).
+int batch_occupancy_fp32(int tx);
+int batch_occupancy_bf16(int tx);
+int batch_occupancy_fp16(int tx);
+inline int batch_ctas_per_sm(int storage, int tx) {
+    return storage == 0 ? batch_occupancy_fp32(tx) : storage == 1 ? batch_occupancy_bf16(tx) : batch_occupancy_fp16(tx);
+}
 cudaError_t prepare_step_fp32();
 cudaError_t prepare_step_bf16();
 cudaError_t prepare_step_fp16();
@@ -35,6 +49,15 @@ inline cudaError_t launch_step_kernel(int storage, const StepLaunch& k, const De
         case 0: return launch_step_fp32(k, p, src, dst, s);
         case 1: return launch_step_bf16(k, p, src, dst, s);
         default: return launch_step_fp16(k, p, src, dst, s);
+    }
+}
+
+inline cudaError_t launch_batch_kernel(int storage, int tx, unsigned grid, const BatchLattice* lats,
+                                       const BatchItem* items, int nitems, int step_parity, cudaStream_t s) {
+    switch (storage) {
+        case 0: return launch_batch_fp32(tx, grid, lats, items, nitems, step_parity, s);
+        case 1: return launch_batch_bf16(tx, grid, lats, items, nitems, step_parity, s);
+        default: return launch_batch_fp16(tx, grid, lats, items, nitems, step_parity, s);
     }
 }
 

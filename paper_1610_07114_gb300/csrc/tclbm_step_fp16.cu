@@ -5,4 +5,6 @@ using ST = __half;
 }
 #define LAUNCH_FN launch_step_fp16
 #define PREPARE_FN prepare_step_fp16
+#define BATCH_FN launch_batch_fp16
+#define BATCH_OCC_FN batch_occupancy_fp16
 #include "tclbm_step_inst.cuh"

@@ -5,4 +5,6 @@ using ST = float;
 }
 #define LAUNCH_FN launch_step_fp32
 #define PREPARE_FN prepare_step_fp32
+#define BATCH_FN launch_batch_fp32
+#define BATCH_OCC_FN batch_occupancy_fp32
 #include "tclbm_step_inst.cuh"

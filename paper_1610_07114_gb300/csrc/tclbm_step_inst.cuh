@@ -67,4 +67,30 @@ cudaError_t LAUNCH_FN(const StepLaunch& k, const DevParams& p, const void* src, 
     }
 }
 
+cudaError_t BATCH_FN(int tx, unsigned grid, const BatchLattice* lats, const BatchItem* items, int nitems,
+                     int step_parity, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    switch (tx) {
+        case 32: tclbm_step_batch<32, ST><<<grid, 32, 0, s>>>(lats, items, nitems, step_parity); break;
+        case 64: tclbm_step_batch<64, ST><<<grid, 64, 0, s>>>(lats, items, nitems, step_parity); break;
+        default: tclbm_step_batch<128, ST><<<grid, 128, 0, s>>>(lats, items, nitems, step_parity); break;
+    }
+    return cudaGetLastError();
+}
+
+int BATCH_OCC_FN(int tx) {
+    int n = 0;
+    cudaError_t e;
+    switch (tx) {
+        case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tclbm_step_batch<32, ST>, 32, 0); break;
+        case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tclbm_step_batch<64, ST>, 64, 0); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tclbm_step_batch<128, ST>, 128, 0); break;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
+
 }  // namespace tclbm

@@ -97,6 +97,21 @@ _lib.tclbm_set_tile.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
 _lib.tclbm_set_tile.restype = ctypes.c_int
 _lib.tclbm_set_kernel.argtypes = [_vp, ctypes.c_int32]
 _lib.tclbm_set_kernel.restype = ctypes.c_int
+_lib.tclbm_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, _vp, ctypes.POINTER(_vp)]
+_lib.tclbm_batch_create.restype = ctypes.c_int
+_lib.tclbm_batch_step.argtypes = [_vp, ctypes.c_int64]
+_lib.tclbm_batch_step.restype = ctypes.c_int
+_lib.tclbm_batch_set_tile.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+_lib.tclbm_batch_set_tile.restype = ctypes.c_int
+_ip = ctypes.POINTER(ctypes.c_int32)
+_lib.tclbm_batch_autotune.argtypes = [_vp, ctypes.c_int32, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_float)]
+_lib.tclbm_batch_autotune.restype = ctypes.c_int
+_lib.tclbm_batch_describe.argtypes = [_vp]
+_lib.tclbm_batch_describe.restype = ctypes.c_char_p
+_lib.tclbm_batch_steps_done.argtypes = [_vp]
+_lib.tclbm_batch_steps_done.restype = ctypes.c_int64
+_lib.tclbm_batch_destroy.argtypes = [_vp]
+_lib.tclbm_batch_destroy.restype = ctypes.c_int
 
 EXPORTED = [name for name in dir(_lib) if name.startswith("tclbm_")]
 
@@ -180,6 +195,41 @@ def tclbm_describe(h) -> str:
 
 def tclbm_destroy(h):
     _check(_lib.tclbm_destroy(h), "tclbm_destroy")
+
+
+def tclbm_batch_create(handles, stream=None):
+    arr = (_vp * len(handles))(*[h.value if isinstance(h, _vp) else h for h in handles])
+    b = _vp()
+    _check(_lib.tclbm_batch_create(arr, len(handles), stream, ctypes.byref(b)), "tclbm_batch_create")
+    return b
+
+
+def tclbm_batch_step(b, n):
+    _check(_lib.tclbm_batch_step(b, int(n)), "tclbm_batch_step")
+
+
+def tclbm_batch_set_tile(b, tx, rows, persistent):
+    _check(_lib.tclbm_batch_set_tile(b, int(tx), int(rows), int(persistent)), "tclbm_batch_set_tile")
+
+
+def tclbm_batch_autotune(b, trial_steps):
+    tx, rows, pers = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    us = ctypes.c_float()
+    _check(_lib.tclbm_batch_autotune(b, int(trial_steps), ctypes.byref(tx), ctypes.byref(rows), ctypes.byref(pers),
+                                     ctypes.byref(us)), "tclbm_batch_autotune")
+    return tx.value, rows.value, pers.value, us.value
+
+
+def tclbm_batch_describe(b) -> str:
+    return _lib.tclbm_batch_describe(b).decode()
+
+
+def tclbm_batch_steps_done(b) -> int:
+    return int(_lib.tclbm_batch_steps_done(b))
+
+
+def tclbm_batch_destroy(b):
+    _check(_lib.tclbm_batch_destroy(b), "tclbm_batch_destroy")
 
 
 # ------------------------------------------------------------------ case dict -> params
@@ -335,6 +385,54 @@ class Lattice:
     def close(self):
         if getattr(self, "handle", None):
             tclbm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """Lattices advanced together by one batched launch per time step (a tclbm_batch)."""
+
+    def __init__(self, lattices, stream=None):
+        import torch
+
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.lattices = list(lattices)  # keeps the handles alive
+        self.stream = stream
+        self.handle = tclbm_batch_create([l.handle for l in self.lattices], ctypes.c_void_p(stream))
+
+    def step(self, n: int = 1):
+        tclbm_batch_step(self.handle, n)
+
+    def set_tile(self, tx: int, rows: int, persistent: bool = True):
+        tclbm_batch_set_tile(self.handle, tx, rows, 1 if persistent else 0)
+
+    def autotune(self, trial_steps: int = 8):
+        """(tx, rows, persistent, us_per_step) of the fastest work-list shape, now selected."""
+        tx, rows, pers, us = tclbm_batch_autotune(self.handle, trial_steps)
+        return tx, rows, bool(pers), us
+
+    @property
+    def steps_done(self) -> int:
+        return tclbm_batch_steps_done(self.handle)
+
+    def describe(self) -> str:
+        return tclbm_batch_describe(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tclbm_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

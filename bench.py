@@ -289,6 +289,52 @@ def bench_batch(args, tclbm, stream):
             "rounding": "stochastic"}
 
 
+def bench_serve(args):
+    """Serving loop on Poisson-arriving requests (Couette, Taylor-Green, Rayleigh-Benard;
+    FP16 deviations with stochastic rounding) against serving each request alone with
+    the plain single-lattice path, both in real time on the same trace."""
+    import torch
+
+    from paper_1610_07114_gb300 import serve
+    from paper_1610_07114_gb300 import workloads as W
+
+    trace = W.serving_trace(duration_s=args.serve_duration, rate=args.serve_rate, seed=42)
+
+    def requests():
+        out = []
+        for i, r in enumerate(trace):
+            case, fields = W.build_request(r)
+            out.append(serve.Request(rid=i, case=case, fields=fields, steps=r["steps"], t_arrival=r["t_arrival"]))
+        return out
+
+    reqs = requests()  # built before either clock starts
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    srv = serve.Server(chunk=args.serve_chunk, keep_results=False)
+    srv.run(reqs)
+    wall = time.perf_counter() - t0
+    served = srv.stats(wall)
+    reqs = requests()
+    torch.cuda.synchronize()
+    _, alone = serve.serve_alone(reqs, keep_results=False)
+    return {"workload": f"serve_poisson_{args.serve_rate:g}per_s_{args.serve_duration:g}s", "requests": len(trace),
+            "nodes_total": int(sum(r["nx"] * r["ny"] for r in trace)), "wall_s": wall, "served": served,
+            "alone": alone, "ratio_LU_per_s": served["LU_per_s"] / alone["LU_per_s"],
+            "p99_ratio_alone_over_served": alone["p99_s"] / served["p99_s"],
+            "storage": "fp16", "rounding": "stochastic", "chunk": args.serve_chunk}
+
+
+def serve_run(args):
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1610_07114_gb300 import build as B
+
+    B.build()
+    print(json.dumps({"serving": bench_serve(args)}))
+    return 0
+
+
 def batch_run(args):
     import torch
 
@@ -407,6 +453,7 @@ def bench_gpu(args):
             pl.close()
 
     batched = None if args.no_batch else bench_batch(args, tclbm, stream)
+    serving = None if args.no_serve else bench_serve(args)
 
     if rank != 0:
         return 0
@@ -440,6 +487,7 @@ def bench_gpu(args):
         "roofline": roofline,
         "roofline_probe": probes,
         "batched": batched,
+        "serving": serving,
         "cpu_baseline": cpu,
         "clocks": clk,
         "gpu_launches": args.steps * (args.chunk + 2),
@@ -482,6 +530,11 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=64)
     ap.add_argument("--batch-tune-steps", type=int, default=6)
     ap.add_argument("--batch-only", action="store_true", help="print only the batched-sweep measurement")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-duration", type=float, default=1.0, help="seconds of Poisson arrivals")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
+    ap.add_argument("--serve-chunk", type=int, default=64)
+    ap.add_argument("--serve-only", action="store_true", help="print only the serving measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -491,6 +544,8 @@ def main():
         return profile_run(args)
     if args.batch_only:
         return batch_run(args)
+    if args.serve_only:
+        return serve_run(args)
     return bench_gpu(args)
 
 

@@ -222,6 +222,16 @@ typedef struct tclbm_batch tclbm_batch;
  * mixed storage formats; ENOMEM if the work list cannot be allocated. */
 tclbm_status tclbm_batch_create(tclbm_lattice* const* lattices, int32_t count, void* stream, tclbm_batch** out);
 
+/* Replace the batch's lattices (count >= 0; same storage format as at creation), keeping
+ * its work-list shape.  Nothing waits for the GPU: the new work list and descriptors
+ * are stream-ordered copies on the batch stream, so steps already queued finish on the
+ * old list.  For serving loops whose set of resident lattices changes while the GPU is
+ * busy.  EINVAL on a NULL or repeated handle or another storage format. */
+tclbm_status tclbm_batch_set_lattices(tclbm_batch* batch, tclbm_lattice* const* lattices, int32_t count);
+
+/* Number of lattices in the batch (-1 for NULL). */
+int32_t tclbm_batch_size(const tclbm_batch* batch);
+
 /* Advance every lattice of the batch by `nsteps` >= 0 time steps (asynchronous). */
 tclbm_status tclbm_batch_step(tclbm_batch* batch, int64_t nsteps);
 

@@ -34,6 +34,14 @@ struct tclbm_batch {
     size_t d_items_bytes = 0;
     int nitems = 0;
     unsigned grid = 0;
+    // pinned staging of uploads, two generations: uploads are stream-ordered copies,
+    // so the host never waits for the kernels in flight
+    struct Staging {
+        void* host = nullptr;
+        size_t bytes = 0;
+        cudaEvent_t used = nullptr;  // the copy out of `host` has executed
+    } stage[2];
+    int gen = 0;
     std::vector<BatchLattice> h_lats;  // last uploaded descriptors
     int64_t steps = 0;                 // batch steps taken (parity of the next launch)
     bool items_valid = false;
@@ -96,20 +104,41 @@ void release(tclbm_batch* B, void*& p, size_t& bytes) {
     bytes = 0;
 }
 
+// Copies `bytes` from `src` into the device array `dst` (grown if needed) on the batch
+// stream, through the pinned staging buffer of this generation.  The previous user of
+// that buffer is two uploads back; its copy has normally long executed.
+tclbm_status upload(tclbm_batch* B, void*& dst, size_t& dst_bytes, const void* src, size_t bytes) {
+    if (bytes == 0) return TCLBM_OK;
+    if (bytes > dst_bytes) {
+        release(B, dst, dst_bytes);  // stream-ordered (caching allocator) or device-synchronising (cudaFree)
+        dst = batch_alloc(B, bytes);
+        if (!dst) return fail(TCLBM_ENOMEM, "batch device allocation of %zu bytes failed", bytes);
+        dst_bytes = bytes;
+    }
+    tclbm_batch::Staging& st = B->stage[B->gen & 1];
+    ++B->gen;
+    CK(cudaEventSynchronize(st.used));
+    if (bytes > st.bytes) {
+        if (st.host) cudaFreeHost(st.host);
+        st.host = nullptr;
+        st.bytes = 0;
+        CK(cudaMallocHost(&st.host, bytes));
+        st.bytes = bytes;
+    }
+    std::memcpy(st.host, src, bytes);
+    CK(cudaMemcpyAsync(dst, st.host, bytes, cudaMemcpyHostToDevice, B->stream));
+    CK(cudaEventRecord(st.used, B->stream));
+    return TCLBM_OK;
+}
+
 tclbm_status upload_items(tclbm_batch* B) {
     if (B->items_valid) return TCLBM_OK;
     std::vector<BatchItem> items;
     make_items(B, items);
-    const size_t bytes = items.size() * sizeof(BatchItem);
-    if (bytes > B->d_items_bytes) {
-        void* p = B->d_items;
-        release(B, p, B->d_items_bytes);
-        B->d_items = (BatchItem*)batch_alloc(B, bytes);
-        if (!B->d_items) return fail(TCLBM_ENOMEM, "work list allocation of %zu bytes failed", bytes);
-        B->d_items_bytes = bytes;
-    }
-    CK(cudaMemcpyAsync(B->d_items, items.data(), bytes, cudaMemcpyHostToDevice, B->stream));
-    CK(cudaStreamSynchronize(B->stream));  // host vector goes out of scope
+    void* d = B->d_items;
+    tclbm_status st = upload(B, d, B->d_items_bytes, items.data(), items.size() * sizeof(BatchItem));
+    B->d_items = (BatchItem*)d;
+    if (st != TCLBM_OK) return st;
     B->nitems = (int)items.size();
     const int per_sm = batch_ctas_per_sm(B->storage, B->tx);
     const long long wave = (long long)B->sms * per_sm;
@@ -138,14 +167,12 @@ tclbm_status upload_lattices(tclbm_batch* B) {
         if (same && std::memcmp(&h[i], &B->h_lats[i], sizeof h[i]) != 0) same = false;
     }
     if (same) return TCLBM_OK;
-    const size_t bytes = n * sizeof(BatchLattice);
-    if (!B->d_lats) {
-        B->d_lats = (BatchLattice*)batch_alloc(B, bytes);
-        if (!B->d_lats) return fail(TCLBM_ENOMEM, "descriptor allocation of %zu bytes failed", bytes);
-        B->d_lats_bytes = bytes;
-    }
-    CK(cudaMemcpyAsync(B->d_lats, h.data(), bytes, cudaMemcpyHostToDevice, B->stream));
-    CK(cudaStreamSynchronize(B->stream));
+    void* d = B->d_lats;
+    const size_t old_bytes = B->d_lats_bytes;
+    tclbm_status st = upload(B, d, B->d_lats_bytes, h.data(), n * sizeof(BatchLattice));
+    B->d_lats = (BatchLattice*)d;
+    if (st != TCLBM_OK) return st;
+    if (B->d_lats_bytes != old_bytes) B->graph_valid = false;  // the array moved
     B->h_lats.swap(h);
     return TCLBM_OK;
 }
@@ -219,6 +246,17 @@ tclbm_status run_steps(tclbm_batch* B, int64_t n) {
     return launch_batch_steps(B, n);
 }
 
+tclbm_status check_lattices(tclbm_lattice* const* lattices, int count, int storage) {
+    for (int i = 0; i < count; ++i) {
+        if (!lattices[i]) return fail(TCLBM_EINVAL, "lattice %d is NULL", i);
+        if (lattices[i]->storage != storage)
+            return fail(TCLBM_EINVAL, "lattice %d has another storage format than the batch", i);
+        for (int j = 0; j < i; ++j)
+            if (lattices[j] == lattices[i]) return fail(TCLBM_EINVAL, "lattice %d appears twice", i);
+    }
+    return TCLBM_OK;
+}
+
 bool valid_shape(int tx, int rows) { return (tx == 32 || tx == 64 || tx == 128) && rows >= 1; }
 
 }  // namespace
@@ -229,13 +267,8 @@ tclbm_status tclbm_batch_create(tclbm_lattice* const* lattices, int32_t count, v
     if (!out) return fail(TCLBM_EINVAL, "out is NULL");
     *out = nullptr;
     if (!lattices || count < 1) return fail(TCLBM_EINVAL, "a batch needs at least one lattice");
-    for (int i = 0; i < count; ++i) {
-        if (!lattices[i]) return fail(TCLBM_EINVAL, "lattice %d is NULL", i);
-        if (lattices[i]->storage != lattices[0]->storage)
-            return fail(TCLBM_EINVAL, "lattice %d has another storage format than lattice 0", i);
-        for (int j = 0; j < i; ++j)
-            if (lattices[j] == lattices[i]) return fail(TCLBM_EINVAL, "lattice %d appears twice", i);
-    }
+    tclbm_status vs = check_lattices(lattices, count, lattices[0]->storage);
+    if (vs != TCLBM_OK) return vs;
     tclbm_batch* B = new (std::nothrow) tclbm_batch;
     if (!B) return fail(TCLBM_ENOMEM, "host allocation failed");
     B->lats.assign(lattices, lattices + count);
@@ -248,6 +281,7 @@ tclbm_status tclbm_batch_create(tclbm_lattice* const* lattices, int32_t count, v
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&B->stage[k].used, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         delete B;
         return cuda_fail(e, "batch setup");
@@ -269,10 +303,30 @@ tclbm_status tclbm_batch_create(tclbm_lattice* const* lattices, int32_t count, v
     return TCLBM_OK;
 }
 
+tclbm_status tclbm_batch_set_lattices(tclbm_batch* B, tclbm_lattice* const* lattices, int32_t count) {
+    if (!B) return fail(TCLBM_EINVAL, "batch is NULL");
+    if (count < 0 || (count > 0 && !lattices)) return fail(TCLBM_EINVAL, "bad lattice list");
+    tclbm_status st = check_lattices(lattices, count, B->storage);
+    if (st != TCLBM_OK) return st;
+    std::vector<tclbm_lattice*> next(lattices, lattices + count);
+    if (next == B->lats) return TCLBM_OK;
+    B->lats.swap(next);
+    B->items_valid = false;
+    st = upload_items(B);
+    if (st == TCLBM_OK) st = upload_lattices(B);
+    return st;
+}
+
+int32_t tclbm_batch_size(const tclbm_batch* B) { return B ? (int32_t)B->lats.size() : -1; }
+
 tclbm_status tclbm_batch_step(tclbm_batch* B, int64_t nsteps) {
     if (!B) return fail(TCLBM_EINVAL, "batch is NULL");
     if (nsteps < 0) return fail(TCLBM_EINVAL, "nsteps must be >= 0");
     if (nsteps == 0) return TCLBM_OK;
+    if (B->lats.empty()) {
+        B->steps += nsteps;
+        return TCLBM_OK;
+    }
     tclbm_status st = join_streams(B, false);
     if (st == TCLBM_OK) st = upload_items(B);
     if (st == TCLBM_OK) st = upload_lattices(B);
@@ -403,6 +457,10 @@ tclbm_status tclbm_batch_destroy(tclbm_batch* B) {
     cudaStreamSynchronize(B->stream);
     if (B->graph) cudaGraphExecDestroy(B->graph);
     if (B->ev) cudaEventDestroy(B->ev);
+    for (auto& st : B->stage) {
+        if (st.used) cudaEventDestroy(st.used);
+        if (st.host) cudaFreeHost(st.host);
+    }
     void* p = B->d_items;
     release(B, p, B->d_items_bytes);
     p = B->d_lats;

@@ -99,6 +99,10 @@ _lib.tclbm_set_kernel.argtypes = [_vp, ctypes.c_int32]
 _lib.tclbm_set_kernel.restype = ctypes.c_int
 _lib.tclbm_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, _vp, ctypes.POINTER(_vp)]
 _lib.tclbm_batch_create.restype = ctypes.c_int
+_lib.tclbm_batch_set_lattices.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int32]
+_lib.tclbm_batch_set_lattices.restype = ctypes.c_int
+_lib.tclbm_batch_size.argtypes = [_vp]
+_lib.tclbm_batch_size.restype = ctypes.c_int32
 _lib.tclbm_batch_step.argtypes = [_vp, ctypes.c_int64]
 _lib.tclbm_batch_step.restype = ctypes.c_int
 _lib.tclbm_batch_set_tile.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
@@ -202,6 +206,15 @@ def tclbm_batch_create(handles, stream=None):
     b = _vp()
     _check(_lib.tclbm_batch_create(arr, len(handles), stream, ctypes.byref(b)), "tclbm_batch_create")
     return b
+
+
+def tclbm_batch_set_lattices(b, handles):
+    arr = (_vp * max(1, len(handles)))(*[h.value if isinstance(h, _vp) else h for h in handles])
+    _check(_lib.tclbm_batch_set_lattices(b, arr, len(handles)), "tclbm_batch_set_lattices")
+
+
+def tclbm_batch_size(b) -> int:
+    return int(_lib.tclbm_batch_size(b))
 
 
 def tclbm_batch_step(b, n):
@@ -410,7 +423,17 @@ class Batch:
             stream = torch.cuda.current_stream().cuda_stream
         self.lattices = list(lattices)  # keeps the handles alive
         self.stream = stream
+        # the batch allocates through the first lattice's allocator hooks: keep them alive
+        self._mem = self.lattices[0]._mem if self.lattices else None
         self.handle = tclbm_batch_create([l.handle for l in self.lattices], ctypes.c_void_p(stream))
+
+    def set_lattices(self, lattices):
+        lattices = list(lattices)
+        tclbm_batch_set_lattices(self.handle, [l.handle for l in lattices])
+        self.lattices = lattices
+
+    def __len__(self):
+        return tclbm_batch_size(self.handle)
 
     def step(self, n: int = 1):
         tclbm_batch_step(self.handle, n)

@@ -265,23 +265,36 @@ def with_walls(case, fields, axis="y", kind="nee", seed=0):
 # --------------------------------------------------------------------------- growth workloads
 
 
+def rb_max_resolved_ra(ny, u_c=0.03, Pr=0.71, w1_max=1.8, RT0=R_DEFAULT):
+    """Largest Rayleigh number a layer of ny rows resolves: the one whose viscosity
+    (rb_gravity) puts w1 = 1 / (nu / RT0 + 1/2) at w1_max.  Ra = Pr (u_c H / nu)^2.
+    Above w1 ~ 1.9 the FP64 oracle itself diverges within a few hundred steps
+    (128 x 64 and 256 x 128 layers, u_c = 0.03 and 0.08); at w1 = 1.8 it runs through
+    the onset into steady convection (64 x 32 and 128 x 64, 40 000 steps)."""
+    nu_min = RT0 * (1.0 / w1_max - 0.5)
+    return Pr * (u_c * (ny - 1) / nu_min) ** 2
+
+
 def batched_rb_sweep(count=256, seed=1234, sizes=((64, 32), (128, 64), (256, 128), (512, 256), (1024, 512)),
                      ra_lo=2e3, ra_hi=1e6, storage="fp16"):
     """Batched Rayleigh-Benard sweep: `count` independent lattices, sizes uniform over
-    `sizes` (aspect 2:1), Ra log-uniform in [ra_lo, ra_hi], Pr = 0.71."""
+    `sizes` (aspect 2:1), Ra log-uniform in [ra_lo, ra_hi] and capped at the lattice's
+    rb_max_resolved_ra (the drawn value is kept as case["Ra_drawn"]), Pr = 0.71."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
         nx, ny = sizes[int(rng.integers(len(sizes)))]
         Ra = float(math.exp(rng.uniform(math.log(ra_lo), math.log(ra_hi))))
-        out.append(rayleigh_benard(nx, ny, Ra=Ra, seed=seed + i, storage=storage))
+        case, fields = rayleigh_benard(nx, ny, Ra=min(Ra, rb_max_resolved_ra(ny)), seed=seed + i, storage=storage)
+        case["Ra_drawn"] = Ra
+        out.append((case, fields))
     return out
 
 
 def serving_trace(duration_s=2.0, rate=200.0, seed=42, scale=1.0, max_nodes=None):
     """Poisson-arriving requests (mean `rate`/s) mixing thermal Couette (32 x 128),
     forced Taylor-Green (256^2 .. 2048^2) and Rayleigh-Benard (128x64 .. 4096x2048,
-    Ra up to 1e7).  Each request asks for a fixed step count.  `scale` shrinks lattice
+    Ra log-uniform up to 1e7, capped at rb_max_resolved_ra of the lattice).  Each request asks for a fixed step count.  `scale` shrinks lattice
     sides (for small test runs); `max_nodes` caps lattice size."""
     rng = np.random.default_rng(seed)
     t = 0.0
@@ -302,7 +315,7 @@ def serving_trace(duration_s=2.0, rate=200.0, seed=42, scale=1.0, max_nodes=None
             e = int(rng.integers(7, 13))
             nx = 2 ** e
             Ra = float(math.exp(rng.uniform(math.log(2e3), math.log(1e7))))
-            spec = ("rayleigh_benard", nx, nx // 2, {"Ra": Ra})
+            spec = ("rayleigh_benard", nx, nx // 2, {"Ra_drawn": Ra})
         name, nx, ny, extra = spec
         nx = max(8, int(nx * scale))
         ny = max(8, int(ny * scale))
@@ -310,6 +323,8 @@ def serving_trace(duration_s=2.0, rate=200.0, seed=42, scale=1.0, max_nodes=None
             while nx * ny > max_nodes:
                 nx //= 2
                 ny //= 2
+        if "Ra_drawn" in extra:  # capped at what the (possibly scaled) lattice resolves
+            extra["Ra"] = min(extra["Ra_drawn"], rb_max_resolved_ra(ny))
         steps = int(rng.choice([200, 500, 1000, 2000]))
         reqs.append({"t_arrival": t, "kind": name, "nx": nx, "ny": ny, "steps": steps, "seed": len(reqs), **extra})
     return reqs

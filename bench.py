@@ -114,29 +114,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def _dist():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
-
-
-def _max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def _barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.barrier()
+from paper_1610_07114_gb300.replicas import barrier as _barrier  # noqa: E402
+from paper_1610_07114_gb300.replicas import dist_env as _dist  # noqa: E402
+from paper_1610_07114_gb300.replicas import max_over_ranks as _max_over_ranks  # noqa: E402
+from paper_1610_07114_gb300.replicas import sum_over_ranks as _sum_over_ranks  # noqa: E402
 
 
 def _workload(args):
@@ -238,12 +219,15 @@ def profile_run(args):
 def bench_batch(args, tclbm, stream):
     """Batched Rayleigh-Benard sweep (256 lattices, 64x32 .. 1024x512, FP16 deviations with
     stochastic rounding): the batched kernel against the plain path (each lattice its own
-    launches), both timed with CUDA events on the same stream over the same lattices."""
+    launches), both timed with CUDA events on the same stream over the same lattices.
+    With several ranks every rank runs its own sweep (weak scaling, no collective on
+    the data path); times are the maximum over ranks."""
     import torch
 
     from paper_1610_07114_gb300 import workloads as W
 
-    cases = W.batched_rb_sweep(count=args.batch_count, storage=args.batch_storage)
+    world, rank, _ = _dist()
+    cases = W.batched_rb_sweep(count=args.batch_count, seed=1234 + 7919 * rank, storage=args.batch_storage)
     lats = [tclbm.Lattice(dict(c, rounding="stochastic"), f, stream=stream.cuda_stream) for c, f in cases]
     nodes = sum(c["nx"] * c["ny"] for c, _ in cases)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
@@ -275,10 +259,11 @@ def bench_batch(args, tclbm, stream):
         l.close()
     torch.cuda.synchronize()
     peak, peak_kind = _peaks()
-    lu = nodes * k
+    lu = _sum_over_ranks(float(nodes * k), world)
+    t_chunk, t_rr, t_batch = (_max_over_ranks(t, world) for t in (t_chunk, t_rr, t_batch))
     plain_best = min(t_chunk, t_rr)
-    achieved = BYTES_PER_LU[args.batch_storage] * lu / t_batch / 1e9
-    return {"workload": f"rb_sweep_{args.batch_count}_{args.batch_storage}", "lattices": args.batch_count,
+    achieved = BYTES_PER_LU[args.batch_storage] * lu / world / t_batch / 1e9  # one GPU's share
+    return {"workload": f"rb_sweep_{args.batch_count}_{args.batch_storage}", "lattices": args.batch_count * world,
             "nodes": nodes, "steps_timed": k, "kernel": desc,
             "autotuned": {"tx": tx, "rows": rows, "persistent": pers, "us_per_step": us},
             "LU_per_s": lu / t_batch, "ms_per_step": t_batch / k * 1e3,
@@ -298,7 +283,8 @@ def bench_serve(args):
     from paper_1610_07114_gb300 import serve
     from paper_1610_07114_gb300 import workloads as W
 
-    trace = W.serving_trace(duration_s=args.serve_duration, rate=args.serve_rate, seed=42)
+    world, rank, _ = _dist()
+    trace = W.serving_trace(duration_s=args.serve_duration, rate=args.serve_rate, seed=42 + rank)
 
     def requests():
         out = []
@@ -309,15 +295,22 @@ def bench_serve(args):
 
     reqs = requests()  # built before either clock starts
     torch.cuda.synchronize()
+    _barrier(world)
     t0 = time.perf_counter()
     srv = serve.Server(chunk=args.serve_chunk, keep_results=False)
     srv.run(reqs)
-    wall = time.perf_counter() - t0
+    wall = _max_over_ranks(time.perf_counter() - t0, world)
     served = srv.stats(wall)
+    served["LU_per_s"] = _sum_over_ranks(float(served["lattice_updates"]), world) / wall
     reqs = requests()
     torch.cuda.synchronize()
+    _barrier(world)
+    t0 = time.perf_counter()
     _, alone = serve.serve_alone(reqs, keep_results=False)
-    return {"workload": f"serve_poisson_{args.serve_rate:g}per_s_{args.serve_duration:g}s", "requests": len(trace),
+    wall_alone = _max_over_ranks(time.perf_counter() - t0, world)
+    alone["LU_per_s"] = _sum_over_ranks(float(alone["lattice_updates"]), world) / wall_alone
+    return {"workload": f"serve_poisson_{args.serve_rate:g}per_s_{args.serve_duration:g}s",
+            "requests_per_rank": len(trace), "ranks": world, "latencies": "rank 0",
             "nodes_total": int(sum(r["nx"] * r["ny"] for r in trace)), "wall_s": wall, "served": served,
             "alone": alone, "ratio_LU_per_s": served["LU_per_s"] / alone["LU_per_s"],
             "p99_ratio_alone_over_served": alone["p99_s"] / served["p99_s"],
@@ -478,7 +471,8 @@ def bench_gpu(args):
         "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "fp32" else f"{args.storage}-dev/f32",
         "data": "synthetic",
-        "config": {"workload": wkey, "nx": args.nx, "ny": args.ny, "Ra": args.ra, "chunk_steps": args.chunk,
+        "config": {"workload": f"rayleigh_benard_{args.nx}x{args.ny}_Ra{args.ra:g}", "nx": args.nx, "ny": args.ny,
+                   "Ra": args.ra, "chunk_steps": args.chunk,
                    "storage": args.storage, "l2": "flushed (256 MiB write) before every timed step; the state itself "
                                                  "is L2-resident within a step",
                    "parallelism": f"replicas x{world}"},

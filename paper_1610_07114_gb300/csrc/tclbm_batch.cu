@@ -33,7 +33,9 @@ struct tclbm_batch {
     BatchItem* d_items = nullptr;
     size_t d_items_bytes = 0;
     int nitems = 0;
-    unsigned grid = 0;
+    // items grouped by collision variant: [first[k], first[k] + count[k]), grid[k] CTAs
+    int first[3] = {0, 0, 0}, count[3] = {0, 0, 0};
+    unsigned grid[3] = {0, 0, 0};
     // pinned staging of uploads, two generations: uploads are stream-ordered copies,
     // so the host never waits for the kernels in flight
     struct Staging {
@@ -45,6 +47,10 @@ struct tclbm_batch {
     std::vector<BatchLattice> h_lats;  // last uploaded descriptors
     int64_t steps = 0;                 // batch steps taken (parity of the next launch)
     bool items_valid = false;
+    // what the uploaded work list was built from: (nx, ny, variant) per lattice in list
+    // order and the shape; a handle's address says nothing (a destroyed lattice's
+    // address can come back for a new one of another size)
+    std::vector<int> items_sig;
     cudaGraphExec_t graph = nullptr;
     bool graph_valid = false;
     cudaEvent_t ev = nullptr;
@@ -60,16 +66,23 @@ int kind_of(const tclbm_lattice* L) {
 
 long long nodes_of(const tclbm_lattice* L) { return (long long)L->prm.nx * L->prm.ny; }
 
-// Work items for the current shape: lattices by decreasing size (longest work first),
-// within a lattice row segments of `rows` rows (the last one takes the remainder, as
-// in the single-lattice kernel) and strips of tx columns, strip index fastest.
-void make_items(const tclbm_batch* B, std::vector<BatchItem>& items) {
+// Work items for the current shape, grouped by collision variant: within a variant,
+// lattices by decreasing size (longest work first); within a lattice row segments of
+// `rows` rows (the last one takes the remainder, as in the single-lattice kernel) and
+// strips of tx columns, strip index fastest.
+void make_items(tclbm_batch* B, std::vector<BatchItem>& items) {
     std::vector<int> order(B->lats.size());
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return nodes_of(B->lats[a]) > nodes_of(B->lats[b]); });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const int ka = kind_of(B->lats[a]), kb = kind_of(B->lats[b]);
+        if (ka != kb) return ka > kb;
+        return nodes_of(B->lats[a]) > nodes_of(B->lats[b]);
+    });
     items.clear();
+    for (int k = 0; k < 3; ++k) B->first[k] = B->count[k] = 0;
     for (int li : order) {
+        const int k = kind_of(B->lats[li]);
+        if (B->count[k] == 0) B->first[k] = (int)items.size();
         const tclbm_params& p = B->lats[li]->prm;
         int nseg = p.ny / B->rows;
         if (nseg < 1) nseg = 1;
@@ -77,8 +90,9 @@ void make_items(const tclbm_batch* B, std::vector<BatchItem>& items) {
         for (int s = 0; s < nseg; ++s) {
             const int y0 = s * B->rows;
             const int y1 = s == nseg - 1 ? p.ny : y0 + B->rows;
-            for (int k = 0; k < nstrip; ++k) items.push_back(BatchItem{li, k * B->tx, y0, y1});
+            for (int c = 0; c < nstrip; ++c) items.push_back(BatchItem{li, c * B->tx, y0, y1});
         }
+        B->count[k] = (int)items.size() - B->first[k];
     }
 }
 
@@ -131,8 +145,27 @@ tclbm_status upload(tclbm_batch* B, void*& dst, size_t& dst_bytes, const void* s
     return TCLBM_OK;
 }
 
+std::vector<int> items_signature(const tclbm_batch* B) {
+    std::vector<int> sig;
+    sig.reserve(3 * B->lats.size() + 3);
+    sig.push_back(B->tx);
+    sig.push_back(B->rows);
+    sig.push_back(B->persistent);
+    for (const tclbm_lattice* L : B->lats) {
+        sig.push_back(L->prm.nx);
+        sig.push_back(L->prm.ny);
+        sig.push_back(kind_of(L));
+    }
+    return sig;
+}
+
 tclbm_status upload_items(tclbm_batch* B) {
     if (B->items_valid) return TCLBM_OK;
+    std::vector<int> sig = items_signature(B);
+    if (!B->items_sig.empty() && sig == B->items_sig) {  // same work list as uploaded
+        B->items_valid = true;
+        return TCLBM_OK;
+    }
     std::vector<BatchItem> items;
     make_items(B, items);
     void* d = B->d_items;
@@ -140,10 +173,12 @@ tclbm_status upload_items(tclbm_batch* B) {
     B->d_items = (BatchItem*)d;
     if (st != TCLBM_OK) return st;
     B->nitems = (int)items.size();
-    const int per_sm = batch_ctas_per_sm(B->storage, B->tx);
-    const long long wave = (long long)B->sms * per_sm;
-    B->grid = (unsigned)(B->persistent ? std::min<long long>(wave, B->nitems) : B->nitems);
+    for (int k = 0; k < 3; ++k) {
+        const long long wave = (long long)B->sms * batch_ctas_per_sm(B->storage, B->tx, k);
+        B->grid[k] = (unsigned)(B->persistent ? std::min<long long>(wave, B->count[k]) : B->count[k]);
+    }
     B->items_valid = true;
+    B->items_sig.swap(sig);
     B->graph_valid = false;
     return TCLBM_OK;
 }
@@ -190,10 +225,20 @@ tclbm_status join_streams(tclbm_batch* B, bool after) {
     return TCLBM_OK;
 }
 
+// One batch step: a launch per collision variant present.
+cudaError_t launch_one_step(const tclbm_batch* B, int parity, cudaStream_t s) {
+    for (int k = 2; k >= 0; --k) {
+        if (B->count[k] == 0) continue;
+        const cudaError_t e = launch_batch_kernel(B->storage, B->tx, k, B->grid[k], B->d_lats,
+                                                  B->d_items + B->first[k], B->count[k], parity, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 tclbm_status launch_batch_steps(tclbm_batch* B, int64_t n) {
     for (int64_t s = 0; s < n; ++s) {
-        const cudaError_t e = launch_batch_kernel(B->storage, B->tx, B->grid, B->d_lats, B->d_items, B->nitems,
-                                                  (int)(B->steps & 1), B->stream);
+        const cudaError_t e = launch_one_step(B, (int)(B->steps & 1), B->stream);
         if (e != cudaSuccess) return cuda_fail(e, "batched step kernel launch");
         ++B->steps;
     }
@@ -212,7 +257,7 @@ tclbm_status build_batch_graph(tclbm_batch* B) {
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         for (int s = 0; s < 2 * kGraphPairs && e == cudaSuccess; ++s)
-            e = launch_batch_kernel(B->storage, B->tx, B->grid, B->d_lats, B->d_items, B->nitems, s & 1, cs);
+            e = launch_one_step(B, s & 1, cs);
         const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (e == cudaSuccess) e = e2;
     }
@@ -308,9 +353,8 @@ tclbm_status tclbm_batch_set_lattices(tclbm_batch* B, tclbm_lattice* const* latt
     if (count < 0 || (count > 0 && !lattices)) return fail(TCLBM_EINVAL, "bad lattice list");
     tclbm_status st = check_lattices(lattices, count, B->storage);
     if (st != TCLBM_OK) return st;
-    std::vector<tclbm_lattice*> next(lattices, lattices + count);
-    if (next == B->lats) return TCLBM_OK;
-    B->lats.swap(next);
+    // always rebuilt from the handles' current sizes (upload_items skips identical lists)
+    B->lats.assign(lattices, lattices + count);
     B->items_valid = false;
     st = upload_items(B);
     if (st == TCLBM_OK) st = upload_lattices(B);
@@ -445,8 +489,11 @@ const char* tclbm_batch_describe(const tclbm_batch* B) {
     if (!B) return "";
     tclbm_batch* M = const_cast<tclbm_batch*>(B);
     const char* st = B->storage == 0 ? "float" : (B->storage == 1 ? "bf16" : "half");
-    snprintf(M->desc, sizeof M->desc, "tclbm_step_batch<%d,%s> lattices %zu items %d grid (%u) block (%d) rows %d%s",
-             B->tx, st, B->lats.size(), B->nitems, B->grid, B->tx, B->rows, B->persistent ? " persistent" : "");
+    snprintf(M->desc, sizeof M->desc,
+             "tclbm_step_batch<%d,%s> lattices %zu items %d (corr %d, thermal %d, athermal %d) grid (%u,%u,%u) "
+             "block (%d) rows %d%s",
+             B->tx, st, B->lats.size(), B->nitems, B->count[2], B->count[1], B->count[0], B->grid[2], B->grid[1],
+             B->grid[0], B->tx, B->rows, B->persistent ? " persistent" : "");
     return B->desc;
 }
 

@@ -25,12 +25,12 @@ struct BatchItem {
     int lat, x0, y0, y1;
 };
 
-// Advances every lattice of a batch by one time step.  CTA b takes items b, b + grid,
-// b + 2 grid, ... (a persistent grid of one wave, or one CTA per item); `step_parity`
-// flips the source copy of every lattice at once.  All lattices share the storage
-// format; each runs the single-lattice strip code, so it evolves bit-identically alone
-// or in a batch.
-template <int TX, class ST>
+// Advances the lattices of one collision variant of a batch by one time step (one
+// launch per variant present; usually one).  CTA b takes items b, b + grid, b + 2 grid,
+// ... (a persistent grid of one wave, or one CTA per item); `step_parity` flips the
+// source copy of every lattice at once.  All lattices share the storage format; each
+// runs the single-lattice strip code, so it evolves bit-identically alone or in a batch.
+template <int TX, class ST, int KIND>
 __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_batch(const BatchLattice* __restrict__ lats,
                                                                  const BatchItem* __restrict__ items, int nitems,
                                                                  int step_parity) {
@@ -51,13 +51,10 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_batch(const BatchLatt
         const int par = sp.parity;
         const ST* src = static_cast<const ST*>(L->buf[par]);
         ST* dst = static_cast<ST*>(const_cast<void*>(L->buf[par ^ 1]));
-        const int kind = L->kind;
-        if (kind == BATCH_THERMAL_CORR)
+        if (KIND == BATCH_THERMAL_CORR)
             strip_corr<TX, ST>(sp, src, dst, it.x0, it.y0, it.y1, ring);
-        else if (kind == BATCH_THERMAL)
-            strip_plain<TX, true, ST>(sp, src, dst, it.x0, it.y0, it.y1);
         else
-            strip_plain<TX, false, ST>(sp, src, dst, it.x0, it.y0, it.y1);
+            strip_plain<TX, KIND == BATCH_THERMAL, ST>(sp, src, dst, it.x0, it.y0, it.y1);
         if (it.x0 == 0 && it.y0 == 0) bump_step_counter(sp);
     }
 }

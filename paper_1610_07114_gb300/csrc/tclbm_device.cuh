@@ -65,6 +65,16 @@ __device__ __forceinline__ uint32_t sr_bits(uint32_t node, uint32_t pair, uint32
     return h;
 }
 
+// Random bits of population pair k from a node's seed: a Weyl step and a short
+// multiply-xorshift finaliser (the seed is already fully mixed).
+__device__ __forceinline__ uint32_t sr_pair_bits(uint32_t seed, uint32_t k) {
+    uint32_t h = seed + k * 0x9E3779B9u;
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    return h;
+}
+
 template <class ST>
 __device__ __forceinline__ uint32_t cvt_rs_pair(float a, float b, uint32_t rbits);
 template <>
@@ -542,6 +552,7 @@ __device__ __forceinline__ void store_node(const DevParams& p, ST* __restrict__ 
         // stochastic rounding, two planes per conversion
         const uint32_t step = p.step_ctr[p.parity];
         const uint32_t node = (uint32_t)(y * p.nx + x);
+        const uint32_t seed = sr_bits(node, 0u, step);  // one full mix per node
         float v[18];
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
@@ -552,7 +563,7 @@ __device__ __forceinline__ void store_node(const DevParams& p, ST* __restrict__ 
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             if (2 * k >= npl) break;
-            const uint32_t d = cvt_rs_pair<ST>(v[2 * k + 1], v[2 * k], sr_bits(node, (uint32_t)k, step));
+            const uint32_t d = cvt_rs_pair<ST>(v[2 * k + 1], v[2 * k], sr_pair_bits(seed, (uint32_t)k));
             const unsigned short lo = (unsigned short)(d & 0xffffu), hi = (unsigned short)(d >> 16);
             reinterpret_cast<unsigned short*>(dst)[(2 * k) * P + o] = lo;
             if (2 * k + 1 < npl) reinterpret_cast<unsigned short*>(dst)[(2 * k + 1) * P + o] = hi;
@@ -656,13 +667,15 @@ __device__ __forceinline__ void strip_corr(const DevParams& p, const ST* __restr
     if (y0 > 0 || p.yper) py_m1 = phiy_only(y0 - 1);
     if (ywall && y1 == ny && y0 >= 2 && y1 - y0 < 3) py_m2 = phiy_only(y0 - 2);
     compute_row(y0, fc, hc, mc, py_0, y0 % 3);
+    __syncthreads();  // the prologue's phi_x row is read by the first collision
 
+    // the lookahead of row r+1 and the collision of row r share one block between
+    // barriers (the collision reads the phi_x row published one barrier earlier)
     for (int r = y0; r < y1; ++r) {
         const bool has_next = (r + 1 < ny) || p.yper;
         if (has_next) compute_row(r + 1, fn, hn, mn, py_p1, (r + 1) % 3);
         float py_p2 = 0.f;
         if (ywall && r == 0) py_p2 = phiy_only(2);
-        __syncthreads();
         if (owns) {
             const float* rw = ring[r % 3];
             const int s = tid + 2;
@@ -684,6 +697,7 @@ __device__ __forceinline__ void strip_corr(const DevParams& p, const ST* __restr
             collide<true>(p, fc, hc, mc, dxv, dyv, fo, ho);
             store_node<ST>(p, dst, xl, r, fo, ho, true);
         }
+        __syncthreads();  // phi_x of row r+1 complete; the buffer of row r-1 free again
         py_m2 = py_m1;
         py_m1 = py_0;
         py_0 = py_p1;

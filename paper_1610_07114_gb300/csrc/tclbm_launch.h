@@ -26,18 +26,20 @@ struct StepLaunch {
 cudaError_t launch_step_fp32(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s);
 cudaError_t launch_step_bf16(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s);
 cudaError_t launch_step_fp16(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s);
-cudaError_t launch_batch_fp32(int tx, unsigned grid, const BatchLattice* lats, const BatchItem* items, int nitems,
-                              int step_parity, cudaStream_t s);
-cudaError_t launch_batch_bf16(int tx, unsigned grid, const BatchLattice* lats, const BatchItem* items, int nitems,
-                              int step_parity, cudaStream_t s);
-cudaError_t launch_batch_fp16(int tx, unsigned grid, const BatchLattice* lats, const BatchItem* items, int nitems,
-                              int step_parity, cudaStream_t s);
-// Resident CTAs per SM of the batched kernel for a tile width (occupancy calculator).
-int batch_occupancy_fp32(int tx);
-int batch_occupancy_bf16(int tx);
-int batch_occupancy_fp16(int tx);
-inline int batch_ctas_per_sm(int storage, int tx) {
-    return storage == 0 ? batch_occupancy_fp32(tx) : storage == 1 ? batch_occupancy_bf16(tx) : batch_occupancy_fp16(tx);
+// Batched step of the items of one collision variant (BATCH_*).
+cudaError_t launch_batch_fp32(int tx, int kind, unsigned grid, const BatchLattice* lats, const BatchItem* items,
+                              int nitems, int step_parity, cudaStream_t s);
+cudaError_t launch_batch_bf16(int tx, int kind, unsigned grid, const BatchLattice* lats, const BatchItem* items,
+                              int nitems, int step_parity, cudaStream_t s);
+cudaError_t launch_batch_fp16(int tx, int kind, unsigned grid, const BatchLattice* lats, const BatchItem* items,
+                              int nitems, int step_parity, cudaStream_t s);
+// Resident CTAs per SM of the batched kernel for a tile width and variant (occupancy calculator).
+int batch_occupancy_fp32(int tx, int kind);
+int batch_occupancy_bf16(int tx, int kind);
+int batch_occupancy_fp16(int tx, int kind);
+inline int batch_ctas_per_sm(int storage, int tx, int kind) {
+    return storage == 0 ? batch_occupancy_fp32(tx, kind)
+                        : storage == 1 ? batch_occupancy_bf16(tx, kind) : batch_occupancy_fp16(tx, kind);
 }
 cudaError_t prepare_step_fp32();
 cudaError_t prepare_step_bf16();
@@ -52,12 +54,12 @@ inline cudaError_t launch_step_kernel(int storage, const StepLaunch& k, const De
     }
 }
 
-inline cudaError_t launch_batch_kernel(int storage, int tx, unsigned grid, const BatchLattice* lats,
+inline cudaError_t launch_batch_kernel(int storage, int tx, int kind, unsigned grid, const BatchLattice* lats,
                                        const BatchItem* items, int nitems, int step_parity, cudaStream_t s) {
     switch (storage) {
-        case 0: return launch_batch_fp32(tx, grid, lats, items, nitems, step_parity, s);
-        case 1: return launch_batch_bf16(tx, grid, lats, items, nitems, step_parity, s);
-        default: return launch_batch_fp16(tx, grid, lats, items, nitems, step_parity, s);
+        case 0: return launch_batch_fp32(tx, kind, grid, lats, items, nitems, step_parity, s);
+        case 1: return launch_batch_bf16(tx, kind, grid, lats, items, nitems, step_parity, s);
+        default: return launch_batch_fp16(tx, kind, grid, lats, items, nitems, step_parity, s);
     }
 }
 

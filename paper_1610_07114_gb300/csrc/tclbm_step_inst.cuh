@@ -67,30 +67,54 @@ cudaError_t LAUNCH_FN(const StepLaunch& k, const DevParams& p, const void* src, 
     }
 }
 
-cudaError_t BATCH_FN(int tx, unsigned grid, const BatchLattice* lats, const BatchItem* items, int nitems,
-                     int step_parity, cudaStream_t s) {
-    if (nitems <= 0) return cudaSuccess;
-    switch (tx) {
-        case 32: tclbm_step_batch<32, ST><<<grid, 32, 0, s>>>(lats, items, nitems, step_parity); break;
-        case 64: tclbm_step_batch<64, ST><<<grid, 64, 0, s>>>(lats, items, nitems, step_parity); break;
-        default: tclbm_step_batch<128, ST><<<grid, 128, 0, s>>>(lats, items, nitems, step_parity); break;
+template <int TX>
+static cudaError_t launch_batch_tx(int kind, unsigned grid, const BatchLattice* lats, const BatchItem* items,
+                                   int nitems, int step_parity, cudaStream_t s) {
+    switch (kind) {
+        case BATCH_THERMAL_CORR:
+            tclbm_step_batch<TX, ST, BATCH_THERMAL_CORR><<<grid, TX, 0, s>>>(lats, items, nitems, step_parity);
+            break;
+        case BATCH_THERMAL:
+            tclbm_step_batch<TX, ST, BATCH_THERMAL><<<grid, TX, 0, s>>>(lats, items, nitems, step_parity);
+            break;
+        default: tclbm_step_batch<TX, ST, BATCH_ATHERMAL><<<grid, TX, 0, s>>>(lats, items, nitems, step_parity);
     }
     return cudaGetLastError();
 }
 
-int BATCH_OCC_FN(int tx) {
+cudaError_t BATCH_FN(int tx, int kind, unsigned grid, const BatchLattice* lats, const BatchItem* items, int nitems,
+                     int step_parity, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    switch (tx) {
+        case 32: return launch_batch_tx<32>(kind, grid, lats, items, nitems, step_parity, s);
+        case 64: return launch_batch_tx<64>(kind, grid, lats, items, nitems, step_parity, s);
+        default: return launch_batch_tx<128>(kind, grid, lats, items, nitems, step_parity, s);
+    }
+}
+
+template <int TX>
+static int occupancy_tx(int kind) {
     int n = 0;
     cudaError_t e;
-    switch (tx) {
-        case 32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tclbm_step_batch<32, ST>, 32, 0); break;
-        case 64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tclbm_step_batch<64, ST>, 64, 0); break;
-        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tclbm_step_batch<128, ST>, 128, 0); break;
-    }
+    if (kind == BATCH_THERMAL_CORR)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tclbm_step_batch<TX, ST, BATCH_THERMAL_CORR>, TX, 0);
+    else if (kind == BATCH_THERMAL)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tclbm_step_batch<TX, ST, BATCH_THERMAL>, TX, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tclbm_step_batch<TX, ST, BATCH_ATHERMAL>, TX, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
     return n > 0 ? n : 1;
+}
+
+int BATCH_OCC_FN(int tx, int kind) {
+    switch (tx) {
+        case 32: return occupancy_tx<32>(kind);
+        case 64: return occupancy_tx<64>(kind);
+        default: return occupancy_tx<128>(kind);
+    }
 }
 
 }  // namespace tclbm

@@ -1,17 +1,19 @@
 // tclbm_tma.cuh -- the fused step with TMA-fed row staging (sm_103a).
 //
 // One thread per CTA streams whole source rows -- all 9 or 18 planes of columns
-// [x0 - M, x0 + TX + M) -- from HBM into an 8-slot shared-memory ring with
-// cp.async.bulk.tensor (one 3-D box per row), signalling an mbarrier per slot.  The
+// [x0 - M, x0 + TX + M) -- from HBM into a shared-memory ring (7 FP32 / 8 16-bit slots)
+// with cp.async.bulk.tensor (one 3-D box per row), signalling an mbarrier per slot.  The
 // compute threads pull their node's populations from the ring (f_q(x, t+1) =
 // f_out_q(x - e_q, t) is a shifted shared-memory read), collide, and store their own
 // node to the destination copy.  Rows are staged several rows ahead of use, so HBM
 // latency is hidden by the copy engine rather than by registers or occupancy.
 //
-// The ring holds source rows r-2 .. r+3 (r+5 with 8 slots) while output row r is
-// processed: the pull of row r needs r-1..r+1, a top-wall node also reads its interior
-// neighbour's pulls (r-2..r), the correction-term lookahead needs row r+1 (sources up
-// to r+2) and a bottom-wall node the one-sided stencil's row 2 (sources up to 3).
+// While output row r is processed: its pull needs source rows r-1..r+1, a top-wall
+// node also its interior neighbour's pulls (r-2..r), the correction-term lookahead row
+// r+1 sources up to r+2, and a bottom-wall node the one-sided stencil's row 2 (sources
+// up to 3).  The correction kernel keeps the lookahead row's pulled populations in
+// registers, so its collision reads no ring row and a slot is free one row after its
+// last lookahead use; the plain kernel pulls at collision time and frees slots later.
 // A launch that finds the error word set returns at once.  Periodic wrap in x: strips whose
 // box crosses x = 0 or x = nx patch the wrapped columns from global memory after the
 // row lands; in y the producer requests the wrapped (or clamped) row directly.
@@ -28,11 +30,11 @@ namespace tclbm {
 
 constexpr long long kWaitNs = 1000000000LL;  // 1 s per wait
 
-// Ring slots: FP32 rows are twice the bytes of 16-bit rows, so FP32 keeps 6 slots
-// (prefetch one row beyond the five in use) to leave room for more CTAs per SM.
+// Ring slots: FP32 rows are twice the bytes of 16-bit rows; 7 FP32 slots (69 KB) keep
+// three CTAs per SM, 8 16-bit slots (43 KB) five.
 template <class ST>
 struct RingSlots {
-    static constexpr int N = sizeof(ST) == 4 ? 6 : 8;
+    static constexpr int N = sizeof(ST) == 4 ? 7 : 8;
 };
 
 __device__ __forceinline__ long long globaltimer_ns() {
@@ -136,6 +138,7 @@ struct RowRing {
     int s_first, s_last;  // source rows this CTA stages
     int issued_to;        // highest source row issued
     int ready_to;         // highest source row waited for (and patched)
+    int freed_to;         // highest source row whose slot was handed back for a refill
     bool patch;           // strip box crosses x = 0 or x = nx on a periodic x axis
     int xb;               // logical column of box index 0
 
@@ -239,6 +242,7 @@ __device__ __forceinline__ void ring_setup(RowRing<TX, THERMAL, ST>& R, unsigned
     R.s_last = s_last;
     R.issued_to = s_first - 1;
     R.ready_to = s_first - 1;
+    R.freed_to = s_first - 1;
     R.xb = x0 - RR::M;
     R.patch = p.xper && (R.xb < 0 || R.xb + RR::BOXW > p.nx);
     if (threadIdx.x == 0) {
@@ -252,15 +256,19 @@ __device__ __forceinline__ void ring_setup(RowRing<TX, THERMAL, ST>& R, unsigned
     }
 }
 
-// thread 0: reuse the slot of a source row nobody reads any more (after a barrier)
+// thread 0: reuse the slots of source rows up to `s_free` that nobody reads any more
+// (called after a barrier); each freed slot takes the row NS further on.
 template <int TX, bool THERMAL, class ST>
 __device__ __forceinline__ void ring_refill(RowRing<TX, THERMAL, ST>& R, const DevParams& p, int s_free) {
-    const int s_new = s_free + RowRing<TX, THERMAL, ST>::NS;
-    if (threadIdx.x == 0 && s_free >= R.s_first && s_new <= R.s_last && s_new > R.issued_to) {
-        // generic-proxy reads (and wrap patches) of this slot happened before the barrier
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        R.issue(p, s_new);
+    constexpr int NS = RowRing<TX, THERMAL, ST>::NS;
+    if (threadIdx.x != 0 || s_free <= R.freed_to) return;
+    // generic-proxy reads (and wrap patches) of these slots happened before the barrier
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    for (int s = R.freed_to + 1; s <= s_free; ++s) {
+        const int s_new = s + NS;
+        if (s_new <= R.s_last && s_new > R.issued_to) R.issue(p, s_new);
     }
+    R.freed_to = s_free;
 }
 
 // Without the correction term (athermal, or thermal with C off).
@@ -309,8 +317,15 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_plain(const DevPa
 // With the correction term: lookahead of one row for the same-time moments, x halo of
 // two columns each side from the ring, the x-derivative through a three-row ring of
 // u_x (1 - theta) in shared memory.
+// Threads per SM the register budget is sized for: FP32 rows fill the shared memory
+// at three CTAs per SM (160 registers each); 16-bit rows run four CTAs of 128.
+template <class ST>
+struct CorrShape {
+    static constexpr int kThreadsPerSM = sizeof(ST) == 4 ? 384 : 512;
+};
+
 template <int TX, class ST>
-__global__ void __launch_bounds__(TX, 640 / TX) tclbm_step_tma_corr(const DevParams p, const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(TX, CorrShape<ST>::kThreadsPerSM / TX) tclbm_step_tma_corr(const DevParams p, const __grid_constant__ CUtensorMap map,
                                                           const ST* __restrict__ src, ST* __restrict__ dst,
                                                           int rows_per_cta, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -360,15 +375,21 @@ __global__ void __launch_bounds__(TX, 640 / TX) tclbm_step_tma_corr(const DevPar
     const bool col_wall_halo = !p.xper && (xh == 0 || xh == nx - 1);
     float py_m2 = 0.f, py_m1 = 0.f, py_0 = 0.f, py_p1 = 0.f;
     Macro mc, mn;
-    // moments of row t (physical row yr, ring slot st): own column (kept) and, for four
-    // lanes, a halo column
-    auto moments_row = [&](int t, int yr, int st, Macro& m, float& py, int buf) {
+    float fc[9], hc[9], fn[9], hn[9];  // pulled populations of rows r and r+1
+    // moments of row t (physical row yr, ring slot st): own column (kept, with its pulled
+    // populations) and, for four lanes, a halo column
+    auto moments_row = [&](int t, int yr, int st, Macro& m, float& py, int buf, float* fk, float* hk) {
         const Slots5 sl = slots_around<RR::NS>(st);
         const bool row_wall = ywall && (t == 0 || t == ny - 1);
         if (own_valid) {
             float f[9], h[9];
             load_node_ring<TX, true, ST>(p, R, sl, xi, xown, yr, row_wall || col_wall_own, f, h);
             m = macro_of<true>(p, f, h, xown, yr);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                fk[q] = f[q];
+                hk[q] = h[q];
+            }
             phix[buf][tid + 2] = phi_x(m);
             py = phi_y(m);
         }
@@ -396,27 +417,24 @@ __global__ void __launch_bounds__(TX, 640 / TX) tclbm_step_tma_corr(const DevPar
     int yr_next = p.yper ? (y0 + 1 == ny ? 0 : y0 + 1) : y0 + 1;  // physical row r + 1
     if (y0 > 0 || p.yper) py_m1 = phiy_row(y0 - 1, y0 == 0 ? ny - 1 : y0 - 1, prev_slot(st));
     if (short_top) py_m2 = phiy_row(y0 - 2, y0 - 2, prev_slot(prev_slot(st)));
-    moments_row(y0, y0, st, mc, py_0, ((y0 % 3) + 3) % 3);
+    moments_row(y0, y0, st, mc, py_0, ((y0 % 3) + 3) % 3, fc, hc);
     int buf_c = ((y0 % 3) + 3) % 3;
 
+    __syncthreads();  // the prologue's phi_x row is read by the first collision
+
+    // Row r: the lookahead of row r+1 (pull, moments, phi) and the collision of row r
+    // (from registers and the phi_x row published one barrier earlier) share one block
+    // between barriers, so the two independent chains interleave.
     for (int r = y0; r < y1; ++r) {
         const bool has_next = (r + 1 < ny) || p.yper;
         const int buf_n = buf_c == 2 ? 0 : buf_c + 1;
         int need = r + 2;
         if (ywall && r == 0) need = 3;
         ok = R.acquire(p, src, need) && ok;
-        if (has_next) moments_row(r + 1, yr_next, next_slot(st), mn, py_p1, buf_n);
+        if (has_next) moments_row(r + 1, yr_next, next_slot(st), mn, py_p1, buf_n, fn, hn);
         float py_p2 = 0.f;
         if (ywall && r == 0) py_p2 = phiy_row(2, 2, next_slot(next_slot(st)));
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicExch(err, 1);
-            R.drain();
-            return;
-        }
-        // source r-3 was last read by the collision of row r-1 (a top-wall neighbour
-        // reads r-3..r-1); the collision of row r below reads r-2..r+1
-        ring_refill<TX, true, ST>(R, p, r - 3);
-        if (owns) {
+        if (owns && ok) {
             const float* rw = phix[buf_c];
             const int s = tid + 2;
             float dxv;
@@ -433,17 +451,27 @@ __global__ void __launch_bounds__(TX, 640 / TX) tclbm_step_tma_corr(const DevPar
                 dyv = 0.5f * (3.0f * py_0 - 4.0f * py_m1 + py_m2);
             else
                 dyv = 0.5f * (py_p1 - py_m1);
-            const Slots5 sl = slots_around<RR::NS>(st);
-            const bool row_wall = ywall && (r == 0 || r == ny - 1);
-            float f[9], h[9], fo[9], ho[9];
-            load_node_ring<TX, true, ST>(p, R, sl, xi, xl, r, row_wall || col_wall_own, f, h);
-            collide<true>(p, f, h, mc, dxv, dyv, fo, ho);
+            float fo[9], ho[9];
+            collide<true>(p, fc, hc, mc, dxv, dyv, fo, ho);
             store_node<ST>(p, dst, xl, r, fo, ho, true);
         }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(err, 1);
+            R.drain();
+            return;
+        }
+        // later rows read sources from r on (a top-wall row r+2 reads its neighbour's
+        // r..r+2): the slot of r-1 is free
+        ring_refill<TX, true, ST>(R, p, r - 1);
         py_m2 = py_m1;
         py_m1 = py_0;
         py_0 = py_p1;
         mc = mn;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            fc[q] = fn[q];
+            hc[q] = hn[q];
+        }
         st = next_slot(st);
         buf_c = buf_n;
         yr_next = (p.yper && yr_next == ny - 1) ? 0 : yr_next + 1;

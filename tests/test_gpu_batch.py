@@ -186,3 +186,25 @@ def test_batch_rejects_bad_arguments(T):
     b.close()
     a.close()
     b16.close()
+
+
+def test_replacing_lattices_rebuilds_the_work_list(T):
+    # A destroyed lattice's handle address can come back for a new lattice of another
+    # size; the batch must rebuild its work list from sizes, not from handle addresses.
+    keep = T.Lattice(*W.random_periodic(40, 24, seed=40))
+    b = T.Batch([keep])
+    sizes = [(24, 16), (70, 36), (16, 8), (96, 40), (33, 21), (64, 64)]
+    prev = None
+    for i, (nx, ny) in enumerate(sizes):
+        case, fields = W.random_periodic(nx, ny, seed=50 + i)
+        lat = T.Lattice(case, fields)
+        lat.set_kernel(1)
+        b.set_lattices([keep, lat])
+        b.step(9)
+        assert_same(case, lat.populations(), alone(T, case, fields, 9))
+        b.set_lattices([keep])
+        lat.close()  # frees the handle; the next iteration's handle may reuse its address
+        prev = (nx, ny)
+    assert prev is not None
+    b.close()
+    keep.close()

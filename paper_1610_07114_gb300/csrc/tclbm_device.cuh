@@ -528,6 +528,52 @@ __device__ __forceinline__ void wall_rebuild(const DevParams& p, int side, int x
     }
 }
 
+// The same, out of line, for kernels whose interior loop must stay compact in the
+// instruction cache (the TMA-fed kernels: wall code inlined at each of their five pull
+// sites cost the FP32 kernel 10 % of its time in a wall-free comparison build; the
+// direct-load kernels run faster with it inlined).  io holds f, h of the wall node and
+// ff, hf of its interior neighbour (36 values); f, h are rewritten.
+template <bool THERMAL>
+__device__ __noinline__ void wall_rebuild_out_of_line(const DevParams* pp, int side, int x, int y, float* io) {
+    float f[9], h[9], ff[9], hf[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        f[q] = io[q];
+        h[q] = io[9 + q];
+        ff[q] = io[18 + q];
+        hf[q] = io[27 + q];
+    }
+    wall_rebuild<THERMAL>(*pp, side, x, y, f, h, ff, hf);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        io[q] = f[q];
+        io[9 + q] = h[q];
+    }
+}
+
+// Call site of the out-of-line rebuild: the node's values are copied into a scratch
+// array, so only the wall branch touches local memory and f, h stay in registers.
+// `p` must be addressable without a copy (a __grid_constant__ kernel parameter or
+// shared memory).
+template <bool THERMAL>
+__device__ __forceinline__ void wall_rebuild_call(const DevParams& p, int side, int x, int y, float* f, float* h,
+                                               const float* ff, const float* hf) {
+    float io[36];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        io[q] = f[q];
+        io[9 + q] = THERMAL ? h[q] : 0.0f;
+        io[18 + q] = ff[q];
+        io[27 + q] = THERMAL ? hf[q] : 0.0f;
+    }
+    wall_rebuild_out_of_line<THERMAL>(&p, side, x, y, io);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        f[q] = io[q];
+        if (THERMAL) h[q] = io[9 + q];
+    }
+}
+
 // Streamed populations of node (x, y) with its wall scheme applied (the state at t+1
 // that Eq. 20 reads), as deviations from the rest state.
 template <bool THERMAL, class ST>

@@ -215,7 +215,7 @@ __device__ __forceinline__ void load_node_ring(const DevParams& p, const RowRing
             else
                 pull_ring<THERMAL, ST, RR::BOXW, RR::SLOT_ELEMS>(R.ring, sl.m1, sl.z, sl.p1,
                                                                   xi + (side == SIDE_XM ? 1 : -1), ff, hf);
-            wall_rebuild<THERMAL>(p, side, x, y, f, h, ff, hf);
+            wall_rebuild_call<THERMAL>(p, side, x, y, f, h, ff, hf);
         }
     }
 }
@@ -273,7 +273,7 @@ __device__ __forceinline__ void ring_refill(RowRing<TX, THERMAL, ST>& R, const D
 
 // Without the correction term (athermal, or thermal with C off).
 template <int TX, bool THERMAL, class ST>
-__global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_plain(const DevParams p, const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_plain(const __grid_constant__ DevParams p, const __grid_constant__ CUtensorMap map,
                                                            const ST* __restrict__ src, ST* __restrict__ dst,
                                                            int rows_per_cta, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -325,7 +325,7 @@ struct CorrShape {
 };
 
 template <int TX, class ST>
-__global__ void __launch_bounds__(TX, CorrShape<ST>::kThreadsPerSM / TX) tclbm_step_tma_corr(const DevParams p, const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(TX, CorrShape<ST>::kThreadsPerSM / TX) tclbm_step_tma_corr(const __grid_constant__ DevParams p, const __grid_constant__ CUtensorMap map,
                                                           const ST* __restrict__ src, ST* __restrict__ dst,
                                                           int rows_per_cta, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];

@@ -176,7 +176,9 @@ constexpr long long kSmallNodes = 1LL << 21;
 void default_launch(const tclbm_params& p, int& tx, int& ty, int& kernel) {
     const long long n = (long long)p.nx * p.ny;
     if (n <= kSmallNodes) {
-        kernel = KERNEL_DIRECT;
+        const bool xper = p.wall[TCLBM_SIDE_XM].kind == TCLBM_WALL_PERIODIC;
+        const bool yper = p.wall[TCLBM_SIDE_YM].kind == TCLBM_WALL_PERIODIC;
+        kernel = tile_kernel_fits(p.nx, p.ny, xper, yper, p.thermal, p.correction) ? KERNEL_TILE : KERNEL_DIRECT;
         tx = p.nx >= 96 ? 64 : 32;
         const long long strips = (p.nx + tx - 1) / tx;
         long long t = (long long)p.ny * strips / (8LL * 152);
@@ -672,7 +674,14 @@ tclbm_status tclbm_set_tile(tclbm_lattice* L, int32_t tx, int32_t ty) {
 
 tclbm_status tclbm_set_kernel(tclbm_lattice* L, int32_t kind) {
     if (!L) return fail(TCLBM_EINVAL, "lattice is NULL");
-    if (kind != KERNEL_TMA && kind != KERNEL_DIRECT) return fail(TCLBM_EINVAL, "kernel kind must be 0 or 1");
+    if (kind != KERNEL_TMA && kind != KERNEL_DIRECT && kind != KERNEL_TILE)
+        return fail(TCLBM_EINVAL, "kernel kind must be 0, 1 or 2");
+    if (kind == KERNEL_TILE && !tile_kernel_fits(L->prm.nx, L->prm.ny, L->dp.xper, L->dp.yper, L->prm.thermal,
+                                                 L->prm.correction))
+        return fail(TCLBM_EUNSUPPORTED,
+                    "2-D tiles need the correction term, nx %% %d != 1 on a walled x axis and ny %% %d != 1 on a "
+                    "walled y axis",
+                    kTileBX, kTileBY);
     L->kernel = kind;
     return TCLBM_OK;
 }

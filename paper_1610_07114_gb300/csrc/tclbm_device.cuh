@@ -780,4 +780,115 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_corr(const DevParams 
     if (blockIdx.x == 0 && blockIdx.y == 0) bump_step_counter(p);
 }
 
+// ---------------------------------------------------------------- 2-D tiles
+
+// The step with the correction term on BX x BY node tiles, one node per thread: each
+// thread pulls its node and, for the 2 (BX + BY) threads with the lowest indices, one
+// halo node (the columns x0-1, x0+BX and rows y0-1, y0+BY around the tile) in the same
+// phase, evaluates the moments and phi = u (1 - 3RT) into shared memory, and after one
+// barrier takes the derivatives and collides.  No thread marches over rows, so a
+// lattice of one short wave finishes its step after a single dependent chain of loads
+// and arithmetic.  Threads of a partial tile on a periodic axis stand in for the
+// wrapped column or row.  Requires nx % BX != 1 unless x is periodic, and ny % BY != 1
+// unless y is periodic (the one-sided derivative at a wall then finds its two
+// neighbours inside the tile or its halo).  Same per-node code as strip_corr.
+template <int BX, int BY, class ST>
+__global__ void __launch_bounds__(BX * BY, 2) tclbm_step_tile(const DevParams p, const ST* __restrict__ src,
+                                                              ST* __restrict__ dst) {
+    __shared__ float phx[BY][BX + 2];  // phi_x of columns x0-1 .. x0+BX
+    __shared__ float phy[BY + 2][BX];  // phi_y of rows y0-1 .. y0+BY
+    const int nx = p.nx, ny = p.ny;
+    const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool owns = x < nx && y < ny;
+    const bool in_x = p.xper || x < nx, in_y = p.yper || y < ny;
+    const int xw = x < nx ? x : x - nx, yw = y < ny ? y : y - ny;  // wrapped (periodic) position
+    const bool node_valid = in_x && in_y && xw < nx && yw < ny;
+
+    // halo node of this thread: t < 2 BY -> column x0-1 / x0+BX at row y0 + t % BY;
+    // t < 2 (BX + BY) -> row y0-1 / y0+BY at column x0 + (t - 2 BY) % BX
+    const int t = threadIdx.x;
+    int hx = 0, hy = 0;
+    bool h_col = false, h_row = false;
+    if (t < 2 * BY) {
+        h_col = true;
+        hx = t < BY ? x0 - 1 : x0 + BX;
+        hy = y0 + t % BY;
+    } else if (t < 2 * (BX + BY)) {
+        h_row = true;
+        const int u = t - 2 * BY;
+        hx = x0 + u % BX;
+        hy = u < BX ? y0 - 1 : y0 + BY;
+    }
+    bool h_valid = h_col || h_row;
+    if (h_valid) {
+        if (p.xper)
+            hx = ((hx % nx) + nx) % nx;
+        else
+            h_valid = hx >= 0 && hx < nx;
+        if (p.yper)
+            hy = ((hy % ny) + ny) % ny;
+        else
+            h_valid = h_valid && hy >= 0 && hy < ny;
+    }
+
+    float f[9], h[9], fh[9], hh[9];
+    if (node_valid) pull<true, ST>(p, src, xw, yw, f, h);
+    if (h_valid) pull<true, ST>(p, src, hx, hy, fh, hh);
+    Macro m;
+    if (node_valid) {
+        const int side = wall_side_of(p, xw, yw);
+        if (side >= 0) {
+            const int nxv = side == SIDE_XM ? 1 : (side == SIDE_XP ? -1 : 0);
+            const int nyv = side == SIDE_YM ? 1 : (side == SIDE_YP ? -1 : 0);
+            float ff[9], hf[9];
+            pull<true, ST>(p, src, xw + nxv, yw + nyv, ff, hf);
+            wall_rebuild<true>(p, side, xw, yw, f, h, ff, hf);
+        }
+        m = macro_of<true>(p, f, h, xw, yw);
+        phx[ty][tx + 1] = phi_x(m);
+        phy[ty + 1][tx] = phi_y(m);
+    }
+    if (h_valid) {
+        const int side = wall_side_of(p, hx, hy);
+        if (side >= 0) {
+            const int nxv = side == SIDE_XM ? 1 : (side == SIDE_XP ? -1 : 0);
+            const int nyv = side == SIDE_YM ? 1 : (side == SIDE_YP ? -1 : 0);
+            float ff[9], hf[9];
+            pull<true, ST>(p, src, hx + nxv, hy + nyv, ff, hf);
+            wall_rebuild<true>(p, side, hx, hy, fh, hh, ff, hf);
+        }
+        const Macro mh = macro_of<true>(p, fh, hh, hx, hy);
+        if (h_col)
+            phx[t % BY][t < BY ? 0 : BX + 1] = phi_x(mh);
+        else
+            phy[t - 2 * BY < BX ? 0 : BY + 1][(t - 2 * BY) % BX] = phi_y(mh);
+    }
+    __syncthreads();
+    if (owns) {
+        const float* rw = phx[ty];
+        const int s = tx + 1;
+        float dxv;
+        if (!p.xper && x == 0)
+            dxv = 0.5f * (-3.0f * rw[s] + 4.0f * rw[s + 1] - rw[s + 2]);
+        else if (!p.xper && x == nx - 1)
+            dxv = 0.5f * (3.0f * rw[s] - 4.0f * rw[s - 1] + rw[s - 2]);
+        else
+            dxv = 0.5f * (rw[s + 1] - rw[s - 1]);
+        const int r = ty + 1;
+        float dyv;
+        if (!p.yper && y == 0)
+            dyv = 0.5f * (-3.0f * phy[r][tx] + 4.0f * phy[r + 1][tx] - phy[r + 2][tx]);
+        else if (!p.yper && y == ny - 1)
+            dyv = 0.5f * (3.0f * phy[r][tx] - 4.0f * phy[r - 1][tx] + phy[r - 2][tx]);
+        else
+            dyv = 0.5f * (phy[r + 1][tx] - phy[r - 1][tx]);
+        float fo[9], ho[9];
+        collide<true>(p, f, h, m, dxv, dyv, fo, ho);
+        store_node<ST>(p, dst, x, y, fo, ho, true);
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0) bump_step_counter(p);
+}
+
 }  // namespace tclbm

@@ -14,7 +14,16 @@ namespace tclbm {
 void set_last_error(const char* msg);
 
 // Kernel variants: the TMA-fed ring (default) and the direct-load marching kernel.
-enum { KERNEL_TMA = 0, KERNEL_DIRECT = 1 };
+// Kernel variants: the TMA-fed ring, the direct-load marching kernel, and 2-D tiles of
+// one node per thread (small lattices with the correction term).
+enum { KERNEL_TMA = 0, KERNEL_DIRECT = 1, KERNEL_TILE = 2 };
+
+// Tile shape of KERNEL_TILE, and whether a lattice can use it (one-sided wall
+// derivatives need nx % BX != 1 on a walled x axis, ny % BY != 1 on a walled y axis).
+constexpr int kTileBX = 32, kTileBY = 8;
+inline bool tile_kernel_fits(int nx, int ny, bool xper, bool yper, bool thermal, bool correction) {
+    return thermal && correction && (xper || nx % kTileBX != 1) && (yper || ny % kTileBY != 1);
+}
 
 struct StepLaunch {
     int thermal, correction, tx, ty, kernel;
@@ -76,6 +85,11 @@ inline void describe_step_kernel(int storage, const StepLaunch& k, const DevPara
     const char* st = storage == 0 ? "float" : (storage == 1 ? "bf16" : "half");
     const dim3 g = step_grid(p, k.tx, k.ty);
     const bool corr = k.thermal && k.correction;
+    if (k.kernel == KERNEL_TILE && corr) {
+        snprintf(out, len, "tclbm_step_tile<%d,%d,%s> grid (%d, %d) block (%d)", kTileBX, kTileBY, st,
+                 (p.nx + kTileBX - 1) / kTileBX, (p.ny + kTileBY - 1) / kTileBY, kTileBX * kTileBY);
+        return;
+    }
     const char* base = k.kernel == KERNEL_TMA ? (corr ? "tclbm_step_tma_corr" : "tclbm_step_tma_plain")
                                               : (corr ? "tclbm_step_corr" : "tclbm_step_plain");
     snprintf(out, len, "%s<%d,%s%s> grid (%u, %u) block (%d) rows/cta %d", base, k.tx,

@@ -32,6 +32,9 @@ static cudaError_t launch_tx(const StepLaunch& k, const DevParams& p0, const voi
             const size_t sm = tma_smem_bytes<TX, false, ST>(false);
             tclbm_step_tma_plain<TX, false, ST><<<grid, TX, sm, s>>>(p, *k.src_map, in, out, k.ty, k.err);
         }
+    } else if (k.kernel == KERNEL_TILE && corr) {
+        const dim3 tgrid((p.nx + kTileBX - 1) / kTileBX, (p.ny + kTileBY - 1) / kTileBY, 1);
+        tclbm_step_tile<kTileBX, kTileBY, ST><<<tgrid, kTileBX * kTileBY, 0, s>>>(p, in, out);
     } else {
         if (corr)
             tclbm_step_corr<TX, ST><<<grid, TX, 0, s>>>(p, in, out, k.ty);

@@ -181,6 +181,7 @@ def test_launch_shapes_are_bit_identical(T):
     states = []
     for tx, ty in ((32, 4), (64, 7), (128, 16), (32, 45), (64, 5), (32, 1), (64, 2), (32, 3)):
         lat = T.Lattice(case, fields)
+        lat.set_kernel(1)  # the marching kernel, whose row segments the tiles change
         lat.set_tile(tx, ty)
         lat.step(25)
         states.append(lat.populations())
@@ -287,3 +288,62 @@ def test_full_size_sampled_nodes(T):
     of, oh = o.update_nodes(xs, ys, f0, h0)
     np.testing.assert_allclose(f1[:, ys, xs].T, of, rtol=0, atol=2e-6)
     np.testing.assert_allclose(h1[:, ys, xs].T, oh, rtol=0, atol=2e-6)
+
+
+TILE_CASES = [
+    ("periodic_corr_partial", *W.random_periodic(150, 45, seed=71, force="accel")),
+    ("periodic_tg_force", *W.random_periodic(70, 37, seed=72, force="taylor_green")),
+    ("rb_zouhe", *W.rayleigh_benard(96, 48, Ra=2e4, seed=73)),
+    ("ywalls_nee", *W.with_walls(*W.random_periodic(64, 19, seed=74, force="accel"), axis="y", kind="nee")),
+    ("xwalls_eq", *W.with_walls(*W.random_periodic(130, 8, seed=75, force="none"), axis="x", kind="equilibrium")),
+    ("couette_narrow", *W.couette()),
+    ("tiny_periodic", *W.random_periodic(3, 5, seed=76, force="accel")),
+]
+
+
+@pytest.mark.parametrize("name,case,fields", TILE_CASES, ids=[c[0] for c in TILE_CASES])
+def test_tile_kernel_agrees_with_the_marching_kernel(T, name, case, fields):
+    # one node per thread on 32 x 8 tiles against row marching: the same per-node code;
+    # wall helpers inlined into another kernel may differ by one ulp (5e-7 absolute)
+    states = []
+    for kind in (2, 1):
+        lat = T.Lattice(case, fields)
+        lat.set_kernel(kind)
+        if kind == 2:
+            assert lat.describe().startswith("tclbm_step_tile")
+        lat.step(41)
+        states.append(lat.populations())
+        lat.close()
+    (fa, ha), (fb, hb) = states
+    walls = any(case["walls"][s]["kind"] != "periodic" for s in ("x-", "x+", "y-", "y+"))
+    if not walls:
+        assert np.array_equal(fa, fb) and np.array_equal(ha, hb)
+    np.testing.assert_allclose(fa, fb, rtol=0, atol=5e-7)
+    np.testing.assert_allclose(ha, hb, rtol=0, atol=5e-7)
+
+
+def test_tile_kernel_matches_the_oracle_and_is_the_small_lattice_default(T):
+    case, fields = W.rayleigh_benard(72, 40, Ra=5e3, seed=77)
+    lat = T.Lattice(case, fields)
+    assert lat.describe().startswith("tclbm_step_tile")
+    lat.step(300)
+    g = lat.moments()
+    lat.close()
+    o = oracle.Oracle(case, fields, threads=8)
+    o.step(300)
+    e = field_errors(g, o.moments(), case["U_ref"])
+    assert e["rho"] <= REL_L2 and e["u"] <= REL_L2 and e["T"] <= REL_L2, e
+
+
+def test_tile_kernel_refuses_lattices_it_cannot_serve(T):
+    # ny % 8 == 1 with y walls: a top-wall row would need a row outside the tile's halo
+    case, fields = W.with_walls(*W.random_periodic(40, 17, seed=78), axis="y", kind="zouhe")
+    lat = T.Lattice(case, fields)
+    assert not lat.describe().startswith("tclbm_step_tile")
+    with pytest.raises(T.TclbmError):
+        lat.set_kernel(2)
+    athermal = T.Lattice(*W.random_periodic(40, 16, seed=79, thermal=False))
+    with pytest.raises(T.TclbmError):
+        athermal.set_kernel(2)
+    lat.close()
+    athermal.close()

@@ -173,27 +173,39 @@ void derive(tclbm_lattice* L) {
 // 4096 x 2048).
 constexpr long long kSmallNodes = 1LL << 21;
 
-void default_launch(const tclbm_params& p, int& tx, int& ty, int& kernel) {
-    const long long n = (long long)p.nx * p.ny;
-    if (n <= kSmallNodes) {
-        const bool xper = p.wall[TCLBM_SIDE_XM].kind == TCLBM_WALL_PERIODIC;
-        const bool yper = p.wall[TCLBM_SIDE_YM].kind == TCLBM_WALL_PERIODIC;
-        kernel = tile_kernel_fits(p.nx, p.ny, xper, yper, p.thermal, p.correction) ? KERNEL_TILE : KERNEL_DIRECT;
+// Launch shape a kernel variant gets by default: (tx, rows per CTA) for the marching
+// kernels, the tile (BX, BY) for KERNEL_TILE.
+void default_shape(const tclbm_params& p, int kernel, int& tx, int& ty) {
+    if (kernel == KERNEL_TILE) {
+        tx = kTileBX;
+        ty = kTileBY;
+    } else if (kernel == KERNEL_DIRECT) {
         tx = p.nx >= 96 ? 64 : 32;
         const long long strips = (p.nx + tx - 1) / tx;
         long long t = (long long)p.ny * strips / (8LL * 152);
         ty = (int)(t < 2 ? 2 : (t > 16 ? 16 : t));
     } else {
-        kernel = KERNEL_TMA;
         tx = p.nx >= 512 ? 128 : (p.nx >= 96 ? 64 : 32);
         ty = 16;
     }
 }
 
-void default_tile(const tclbm_params& p, int& tx, int& ty) {
-    int k;
-    default_launch(p, tx, ty, k);
+bool tile_fits(const tclbm_params& p, int bx, int by) {
+    const bool xper = p.wall[TCLBM_SIDE_XM].kind == TCLBM_WALL_PERIODIC;
+    const bool yper = p.wall[TCLBM_SIDE_YM].kind == TCLBM_WALL_PERIODIC;
+    return tile_kernel_fits(p.nx, p.ny, xper, yper, p.thermal, p.correction, bx, by);
 }
+
+void default_launch(const tclbm_params& p, int& tx, int& ty, int& kernel) {
+    const long long n = (long long)p.nx * p.ny;
+    if (n <= kSmallNodes)
+        kernel = tile_fits(p, kTileBX, kTileBY) ? KERNEL_TILE : KERNEL_DIRECT;
+    else
+        kernel = KERNEL_TMA;
+    default_shape(p, kernel, tx, ty);
+}
+
+void default_tile(const tclbm_params& p, int kernel, int& tx, int& ty) { default_shape(p, kernel, tx, ty); }
 
 // ------------------------------------------------------------------ small kernels
 
@@ -664,11 +676,17 @@ int64_t tclbm_steps_done(const tclbm_lattice* L) { return L ? L->steps : -1; }
 tclbm_status tclbm_set_tile(tclbm_lattice* L, int32_t tx, int32_t ty) {
     if (!L) return fail(TCLBM_EINVAL, "lattice is NULL");
     int dtx, dty;
-    default_tile(L->prm, dtx, dty);
-    if (tx != 0 && tx != 32 && tx != 64 && tx != 128) return fail(TCLBM_EINVAL, "tx must be 0, 32, 64 or 128");
-    if (ty < 0) return fail(TCLBM_EINVAL, "ty must be 0 or >= 1");
-    L->tx = tx ? tx : dtx;
-    L->ty = ty ? ty : dty;
+    default_tile(L->prm, L->kernel, dtx, dty);
+    const int ntx = tx ? tx : dtx, nty = ty ? ty : dty;
+    if (L->kernel == KERNEL_TILE) {
+        if (!tile_fits(L->prm, ntx, nty))
+            return fail(TCLBM_EINVAL, "tile shape %dx%d is not available for this lattice", ntx, nty);
+    } else {
+        if (tx != 0 && tx != 32 && tx != 64 && tx != 128) return fail(TCLBM_EINVAL, "tx must be 0, 32, 64 or 128");
+        if (ty < 0) return fail(TCLBM_EINVAL, "ty must be 0 or >= 1");
+    }
+    L->tx = ntx;
+    L->ty = nty;
     return TCLBM_OK;
 }
 
@@ -676,12 +694,12 @@ tclbm_status tclbm_set_kernel(tclbm_lattice* L, int32_t kind) {
     if (!L) return fail(TCLBM_EINVAL, "lattice is NULL");
     if (kind != KERNEL_TMA && kind != KERNEL_DIRECT && kind != KERNEL_TILE)
         return fail(TCLBM_EINVAL, "kernel kind must be 0, 1 or 2");
-    if (kind == KERNEL_TILE && !tile_kernel_fits(L->prm.nx, L->prm.ny, L->dp.xper, L->dp.yper, L->prm.thermal,
-                                                 L->prm.correction))
+    if (kind == KERNEL_TILE && !tile_fits(L->prm, kTileBX, kTileBY))
         return fail(TCLBM_EUNSUPPORTED,
                     "2-D tiles need the correction term, nx %% %d != 1 on a walled x axis and ny %% %d != 1 on a "
                     "walled y axis",
                     kTileBX, kTileBY);
+    if (kind != L->kernel) default_shape(L->prm, kind, L->tx, L->ty);
     L->kernel = kind;
     return TCLBM_OK;
 }

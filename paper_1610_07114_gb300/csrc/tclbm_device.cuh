@@ -793,8 +793,10 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_corr(const DevParams 
 // unless y is periodic (the one-sided derivative at a wall then finds its two
 // neighbours inside the tile or its halo).  Same per-node code as strip_corr.
 template <int BX, int BY, class ST>
-__global__ void __launch_bounds__(BX * BY, 2) tclbm_step_tile(const DevParams p, const ST* __restrict__ src,
+__global__ void __launch_bounds__(BX * BY, 512 / (BX * BY)) tclbm_step_tile(const DevParams p, const ST* __restrict__ src,
                                                               ST* __restrict__ dst) {
+    static_assert(2 * (BX + BY) <= BX * BY, "every halo node needs a thread");
+    static_assert(BX >= 3 && BY >= 3, "a wall's one-sided derivative reads two nodes inside the tile");
     __shared__ float phx[BY][BX + 2];  // phi_x of columns x0-1 .. x0+BX
     __shared__ float phy[BY + 2][BX];  // phi_y of rows y0-1 .. y0+BY
     const int nx = p.nx, ny = p.ny;

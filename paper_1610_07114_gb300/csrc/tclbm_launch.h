@@ -18,13 +18,18 @@ void set_last_error(const char* msg);
 // one node per thread (small lattices with the correction term).
 enum { KERNEL_TMA = 0, KERNEL_DIRECT = 1, KERNEL_TILE = 2 };
 
-// Tile shape of KERNEL_TILE, and whether a lattice can use it (one-sided wall
-// derivatives need nx % BX != 1 on a walled x axis, ny % BY != 1 on a walled y axis).
-constexpr int kTileBX = 32, kTileBY = 8;
-inline bool tile_kernel_fits(int nx, int ny, bool xper, bool yper, bool thermal, bool correction) {
-    return thermal && correction && (xper || nx % kTileBX != 1) && (yper || ny % kTileBY != 1);
+// Tile shapes of KERNEL_TILE (set through tclbm_set_tile as (BX, BY)), and whether a
+// lattice can use one (one-sided wall derivatives need nx % BX != 1 on a walled x axis
+// and ny % BY != 1 on a walled y axis).
+constexpr int kTileBX = 32, kTileBY = 4;  // default shape (fastest from 256x128 to 2048x1024)
+inline bool tile_shape_valid(int bx, int by) {
+    return (bx == 16 && (by == 4 || by == 8)) || (bx == 32 && (by == 4 || by == 8 || by == 16)) ||
+           (bx == 64 && (by == 4 || by == 8)) || (bx == 128 && by == 4);
 }
-
+inline bool tile_kernel_fits(int nx, int ny, bool xper, bool yper, bool thermal, bool correction, int bx = kTileBX,
+                             int by = kTileBY) {
+    return thermal && correction && tile_shape_valid(bx, by) && (xper || nx % bx != 1) && (yper || ny % by != 1);
+}
 struct StepLaunch {
     int thermal, correction, tx, ty, kernel;
     const CUtensorMap* src_map;  // tensor map of the source copy (KERNEL_TMA)
@@ -86,8 +91,8 @@ inline void describe_step_kernel(int storage, const StepLaunch& k, const DevPara
     const dim3 g = step_grid(p, k.tx, k.ty);
     const bool corr = k.thermal && k.correction;
     if (k.kernel == KERNEL_TILE && corr) {
-        snprintf(out, len, "tclbm_step_tile<%d,%d,%s> grid (%d, %d) block (%d)", kTileBX, kTileBY, st,
-                 (p.nx + kTileBX - 1) / kTileBX, (p.ny + kTileBY - 1) / kTileBY, kTileBX * kTileBY);
+        snprintf(out, len, "tclbm_step_tile<%d,%d,%s> grid (%d, %d) block (%d)", k.tx, k.ty, st,
+                 (p.nx + k.tx - 1) / k.tx, (p.ny + k.ty - 1) / k.ty, k.tx * k.ty);
         return;
     }
     const char* base = k.kernel == KERNEL_TMA ? (corr ? "tclbm_step_tma_corr" : "tclbm_step_tma_plain")

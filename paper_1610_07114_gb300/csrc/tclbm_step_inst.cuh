@@ -13,6 +13,24 @@ static cudaError_t allow_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <int BX, int BY>
+static cudaError_t launch_tile_shape(const DevParams& p, const ST* in, ST* out, cudaStream_t s) {
+    const dim3 grid((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, 1);
+    tclbm_step_tile<BX, BY, ST><<<grid, BX * BY, 0, s>>>(p, in, out);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_tile(int bx, int by, const DevParams& p, const ST* in, ST* out, cudaStream_t s) {
+    if (bx == 16 && by == 4) return launch_tile_shape<16, 4>(p, in, out, s);
+    if (bx == 16 && by == 8) return launch_tile_shape<16, 8>(p, in, out, s);
+    if (bx == 32 && by == 8) return launch_tile_shape<32, 8>(p, in, out, s);
+    if (bx == 32 && by == 16) return launch_tile_shape<32, 16>(p, in, out, s);
+    if (bx == 64 && by == 4) return launch_tile_shape<64, 4>(p, in, out, s);
+    if (bx == 64 && by == 8) return launch_tile_shape<64, 8>(p, in, out, s);
+    if (bx == 128 && by == 4) return launch_tile_shape<128, 4>(p, in, out, s);
+    return launch_tile_shape<32, 4>(p, in, out, s);
+}
+
 template <int TX>
 static cudaError_t launch_tx(const StepLaunch& k, const DevParams& p0, const void* src, void* dst, cudaStream_t s) {
     DevParams p = p0;
@@ -33,8 +51,7 @@ static cudaError_t launch_tx(const StepLaunch& k, const DevParams& p0, const voi
             tclbm_step_tma_plain<TX, false, ST><<<grid, TX, sm, s>>>(p, *k.src_map, in, out, k.ty, k.err);
         }
     } else if (k.kernel == KERNEL_TILE && corr) {
-        const dim3 tgrid((p.nx + kTileBX - 1) / kTileBX, (p.ny + kTileBY - 1) / kTileBY, 1);
-        tclbm_step_tile<kTileBX, kTileBY, ST><<<tgrid, kTileBX * kTileBY, 0, s>>>(p, in, out);
+        return launch_tile(k.tx, k.ty, p, in, out, s);
     } else {
         if (corr)
             tclbm_step_corr<TX, ST><<<grid, TX, 0, s>>>(p, in, out, k.ty);

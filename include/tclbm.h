@@ -190,14 +190,20 @@ const char* tclbm_last_error(void);
  * profiling ("tclbm_step_kernel<...> grid (gx, gy) block (bx)"). */
 const char* tclbm_describe(const tclbm_lattice* lat);
 
-/* Launch-shape override for tuning: tile width tx (32, 64 or 128 nodes) and rows per
- * CTA ty (>= 1); 0 keeps the library's choice. */
+/* Launch-shape override for tuning; 0 keeps the library's choice.  Kernel variants 0
+ * and 1: strip width tx (32, 64 or 128 nodes) and rows per CTA ty (>= 1).  Variant 2:
+ * the tile (tx, ty) = (BX, BY), one of 16x4, 16x8, 32x4, 32x8, 32x16, 64x4, 64x8,
+ * 128x4, subject to the variant's size rule (EINVAL otherwise). */
 tclbm_status tclbm_set_tile(tclbm_lattice* lat, int32_t tx, int32_t ty);
 
 /* Step kernel variant: 0 = rows staged into shared memory by the tensor-memory
- * accelerator, 1 = direct loads.  The library picks per lattice size (direct loads for
- * lattices that fit in L2).  Interior nodes evolve bit-identically under both; wall
- * nodes may differ in the last bit (multiply-add contraction). */
+ * accelerator, 1 = direct loads marching up strips of rows, 2 = direct loads on 2-D
+ * tiles, one node per thread (thermal lattices with the correction term; on a walled x
+ * axis nx % BX != 1 and on a walled y axis ny % BY != 1, else TCLBM_EUNSUPPORTED).  The
+ * library picks per lattice size: 2 (or 1 where 2 does not apply) up to 2,097,152
+ * nodes, 0 above.  Interior nodes evolve bit-identically under all variants; wall
+ * nodes may differ in the last bit (multiply-add contraction).  Changing the variant
+ * resets the launch shape to that variant's default.  EINVAL for other values. */
 tclbm_status tclbm_set_kernel(tclbm_lattice* lat, int32_t kind);
 
 /* ------------------------------------------------------------------ batches

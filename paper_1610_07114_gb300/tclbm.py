@@ -385,7 +385,8 @@ class Lattice:
         tclbm_set_tile(self.handle, tx, ty)
 
     def set_kernel(self, kind: int):
-        """0: TMA-staged rows (default); 1: direct loads."""
+        """0: TMA-staged rows; 1: direct loads, row strips; 2: direct loads, 2-D tiles
+        (one node per thread).  The library picks by lattice size."""
         tclbm_set_kernel(self.handle, kind)
 
     def set_stream(self, stream):

@@ -783,7 +783,7 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_corr(const DevParams 
 // ---------------------------------------------------------------- 2-D tiles
 
 // The step with the correction term on BX x BY node tiles, one node per thread: each
-// thread pulls its node and, for the 2 (BX + BY) threads with the lowest indices, one
+// thread pulls its node and, for the 2 (BX + BY) threads with the highest indices, one
 // halo node (the columns x0-1, x0+BX and rows y0-1, y0+BY around the tile) in the same
 // phase, evaluates the moments and phi = u (1 - 3RT) into shared memory, and after one
 // barrier takes the derivatives and collides.  No thread marches over rows, so a
@@ -808,20 +808,22 @@ __global__ void __launch_bounds__(BX * BY, 512 / (BX * BY)) tclbm_step_tile(cons
     const int xw = x < nx ? x : x - nx, yw = y < ny ? y : y - ny;  // wrapped (periodic) position
     const bool node_valid = in_x && in_y && xw < nx && yw < ny;
 
-    // halo node of this thread: t < 2 BY -> column x0-1 / x0+BX at row y0 + t % BY;
-    // t < 2 (BX + BY) -> row y0-1 / y0+BY at column x0 + (t - 2 BY) % BX
-    const int t = threadIdx.x;
+    // halo node of this thread, taken by the last 2 (BX + BY) threads, so that the halo
+    // columns of a wall row land in another warp than the wall row's own nodes: halo
+    // index u < 2 BY -> column x0-1 / x0+BX at row y0 + u % BY; u < 2 (BX + BY) -> row
+    // y0-1 / y0+BY at column x0 + (u - 2 BY) % BX
+    const int u = (int)threadIdx.x - (BX * BY - 2 * (BX + BY));
     int hx = 0, hy = 0;
     bool h_col = false, h_row = false;
-    if (t < 2 * BY) {
+    if (u >= 0 && u < 2 * BY) {
         h_col = true;
-        hx = t < BY ? x0 - 1 : x0 + BX;
-        hy = y0 + t % BY;
-    } else if (t < 2 * (BX + BY)) {
+        hx = u < BY ? x0 - 1 : x0 + BX;
+        hy = y0 + u % BY;
+    } else if (u >= 2 * BY) {
         h_row = true;
-        const int u = t - 2 * BY;
-        hx = x0 + u % BX;
-        hy = u < BX ? y0 - 1 : y0 + BY;
+        const int v = u - 2 * BY;
+        hx = x0 + v % BX;
+        hy = v < BX ? y0 - 1 : y0 + BY;
     }
     bool h_valid = h_col || h_row;
     if (h_valid) {
@@ -835,37 +837,33 @@ __global__ void __launch_bounds__(BX * BY, 512 / (BX * BY)) tclbm_step_tile(cons
             h_valid = h_valid && hy >= 0 && hy < ny;
     }
 
-    float f[9], h[9], fh[9], hh[9];
+    // every pull in one phase: own node, halo node, and the interior neighbours that
+    // the wall schemes of a wall node (own or halo) read
+    const int side_o = node_valid ? wall_side_of(p, xw, yw) : -1;
+    const int side_h = h_valid ? wall_side_of(p, hx, hy) : -1;
+    float f[9], h[9], fh[9], hh[9], fn[9], hn[9], fhn[9], hhn[9];
     if (node_valid) pull<true, ST>(p, src, xw, yw, f, h);
     if (h_valid) pull<true, ST>(p, src, hx, hy, fh, hh);
+    if (side_o >= 0)
+        pull<true, ST>(p, src, xw + (side_o == SIDE_XM ? 1 : (side_o == SIDE_XP ? -1 : 0)),
+                       yw + (side_o == SIDE_YM ? 1 : (side_o == SIDE_YP ? -1 : 0)), fn, hn);
+    if (side_h >= 0)
+        pull<true, ST>(p, src, hx + (side_h == SIDE_XM ? 1 : (side_h == SIDE_XP ? -1 : 0)),
+                       hy + (side_h == SIDE_YM ? 1 : (side_h == SIDE_YP ? -1 : 0)), fhn, hhn);
     Macro m;
     if (node_valid) {
-        const int side = wall_side_of(p, xw, yw);
-        if (side >= 0) {
-            const int nxv = side == SIDE_XM ? 1 : (side == SIDE_XP ? -1 : 0);
-            const int nyv = side == SIDE_YM ? 1 : (side == SIDE_YP ? -1 : 0);
-            float ff[9], hf[9];
-            pull<true, ST>(p, src, xw + nxv, yw + nyv, ff, hf);
-            wall_rebuild<true>(p, side, xw, yw, f, h, ff, hf);
-        }
+        if (side_o >= 0) wall_rebuild<true>(p, side_o, xw, yw, f, h, fn, hn);
         m = macro_of<true>(p, f, h, xw, yw);
         phx[ty][tx + 1] = phi_x(m);
         phy[ty + 1][tx] = phi_y(m);
     }
     if (h_valid) {
-        const int side = wall_side_of(p, hx, hy);
-        if (side >= 0) {
-            const int nxv = side == SIDE_XM ? 1 : (side == SIDE_XP ? -1 : 0);
-            const int nyv = side == SIDE_YM ? 1 : (side == SIDE_YP ? -1 : 0);
-            float ff[9], hf[9];
-            pull<true, ST>(p, src, hx + nxv, hy + nyv, ff, hf);
-            wall_rebuild<true>(p, side, hx, hy, fh, hh, ff, hf);
-        }
+        if (side_h >= 0) wall_rebuild<true>(p, side_h, hx, hy, fh, hh, fhn, hhn);
         const Macro mh = macro_of<true>(p, fh, hh, hx, hy);
         if (h_col)
-            phx[t % BY][t < BY ? 0 : BX + 1] = phi_x(mh);
+            phx[u % BY][u < BY ? 0 : BX + 1] = phi_x(mh);
         else
-            phy[t - 2 * BY < BX ? 0 : BY + 1][(t - 2 * BY) % BX] = phi_y(mh);
+            phy[u - 2 * BY < BX ? 0 : BY + 1][(u - 2 * BY) % BX] = phi_y(mh);
     }
     __syncthreads();
     if (owns) {

@@ -799,6 +799,10 @@ __global__ void __launch_bounds__(BX * BY, 512 / (BX * BY)) tclbm_step_tile(cons
     static_assert(BX >= 3 && BY >= 3, "a wall's one-sided derivative reads two nodes inside the tile");
     __shared__ float phx[BY][BX + 2];  // phi_x of columns x0-1 .. x0+BX
     __shared__ float phy[BY + 2][BX];  // phi_y of rows y0-1 .. y0+BY
+    // programmatic dependent launch: wait for the previous step's grid (its writes are
+    // this step's source), then let the next step's grid be scheduled behind this one
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int nx = p.nx, ny = p.ny;
     const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;

@@ -15,9 +15,20 @@ static cudaError_t allow_smem(K kernel, size_t bytes) {
 
 template <int BX, int BY>
 static cudaError_t launch_tile_shape(const DevParams& p, const ST* in, ST* out, cudaStream_t s) {
-    const dim3 grid((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, 1);
-    tclbm_step_tile<BX, BY, ST><<<grid, BX * BY, 0, s>>>(p, in, out);
-    return cudaGetLastError();
+    // programmatic dependent launch: the next step's grid is scheduled while this one
+    // runs (the kernel waits for its predecessor before touching memory)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, 1);
+    cfg.blockDim = dim3(BX * BY, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, tclbm_step_tile<BX, BY, ST>, p, in, out);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 static cudaError_t launch_tile(int bx, int by, const DevParams& p, const ST* in, ST* out, cudaStream_t s) {

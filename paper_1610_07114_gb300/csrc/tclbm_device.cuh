@@ -793,19 +793,12 @@ __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_corr(const DevParams 
 // unless y is periodic (the one-sided derivative at a wall then finds its two
 // neighbours inside the tile or its halo).  Same per-node code as strip_corr.
 template <int BX, int BY, class ST>
-__global__ void __launch_bounds__(BX * BY, 512 / (BX * BY)) tclbm_step_tile(const DevParams p, const ST* __restrict__ src,
-                                                              ST* __restrict__ dst) {
+__device__ __forceinline__ void tile_step(const DevParams& p, const ST* __restrict__ src, ST* __restrict__ dst,
+                                          int x0, int y0, float (*phx)[BX + 2], float (*phy)[BX]) {
     static_assert(2 * (BX + BY) <= BX * BY, "every halo node needs a thread");
     static_assert(BX >= 3 && BY >= 3, "a wall's one-sided derivative reads two nodes inside the tile");
-    __shared__ float phx[BY][BX + 2];  // phi_x of columns x0-1 .. x0+BX
-    __shared__ float phy[BY + 2][BX];  // phi_y of rows y0-1 .. y0+BY
-    // programmatic dependent launch: wait for the previous step's grid (its writes are
-    // this step's source), then let the next step's grid be scheduled behind this one
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int nx = p.nx, ny = p.ny;
     const int tx = threadIdx.x % BX, ty = threadIdx.x / BX;
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
     const int x = x0 + tx, y = y0 + ty;
     const bool owns = x < nx && y < ny;
     const bool in_x = p.xper || x < nx, in_y = p.yper || y < ny;
@@ -892,6 +885,19 @@ __global__ void __launch_bounds__(BX * BY, 512 / (BX * BY)) tclbm_step_tile(cons
         collide<true>(p, f, h, m, dxv, dyv, fo, ho);
         store_node<ST>(p, dst, x, y, fo, ho, true);
     }
+}
+
+// One lattice: CTA (bx, by) takes the tile at (bx BX, by BY).
+template <int BX, int BY, class ST>
+__global__ void __launch_bounds__(BX * BY, 512 / (BX * BY)) tclbm_step_tile(const DevParams p, const ST* __restrict__ src,
+                                                              ST* __restrict__ dst) {
+    __shared__ float phx[BY][BX + 2];  // phi_x of columns x0-1 .. x0+BX
+    __shared__ float phy[BY + 2][BX];  // phi_y of rows y0-1 .. y0+BY
+    // programmatic dependent launch: wait for the previous step's grid (its writes are
+    // this step's source), then let the next step's grid be scheduled behind this one
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    tile_step<BX, BY, ST>(p, src, dst, blockIdx.x * BX, blockIdx.y * BY, phx, phy);
     if (blockIdx.x == 0 && blockIdx.y == 0) bump_step_counter(p);
 }
 

@@ -653,7 +653,7 @@ tclbm_status tclbm_create(const tclbm_params* params, tclbm_alloc_fn alloc, tclb
 tclbm_status tclbm_destroy(tclbm_lattice* L) {
     if (!L) return TCLBM_OK;
     if (L->graph) cudaGraphExecDestroy(L->graph);
-    if (L->stream || true) cudaStreamSynchronize(L->stream);
+    cudaStreamSynchronize(L->stream);  // work queued on the handle may still use its memory
     dev_free(L, L->buf[0], L->buf_bytes);
     dev_free(L, L->buf[1], L->buf_bytes);
     dev_free(L, L->tables, L->tables_bytes);

@@ -458,15 +458,20 @@ tclbm_status tclbm_batch_autotune(tclbm_batch* B, int32_t trial_steps, int32_t* 
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     // restore the state; the batch's parity is back where it was (even trial lengths)
+    cudaError_t re = cudaSuccess;  // first failure of the restore copies
     {
         size_t off = 0;
         for (tclbm_lattice* L : B->lats) {
-            cudaMemcpyAsync(L->buf[L->cur], backup + off, L->buf_bytes, cudaMemcpyDeviceToDevice, B->stream);
-            cudaMemcpyAsync(L->err, backup + off + L->buf_bytes, 256, cudaMemcpyDeviceToDevice, B->stream);
+            cudaError_t e1 = cudaMemcpyAsync(L->buf[L->cur], backup + off, L->buf_bytes, cudaMemcpyDeviceToDevice,
+                                             B->stream);
+            cudaError_t e2 = cudaMemcpyAsync(L->err, backup + off + L->buf_bytes, 256, cudaMemcpyDeviceToDevice,
+                                             B->stream);
+            if (re == cudaSuccess) re = e1 != cudaSuccess ? e1 : e2;
             off += L->buf_bytes + 256;
         }
     }
-    const cudaError_t se = cudaStreamSynchronize(B->stream);
+    cudaError_t se = cudaStreamSynchronize(B->stream);
+    if (se == cudaSuccess) se = re;
     release(B, backup_mem, total);
     B->steps = keep_steps;
     if (st != TCLBM_OK) return st;

@@ -290,6 +290,59 @@ def test_full_size_sampled_nodes(T):
     np.testing.assert_allclose(h1[:, ys, xs].T, oh, rtol=0, atol=2e-6)
 
 
+def test_full_size_sampled_nodes_fp16_stochastic(T):
+    # the same lattice in 16-bit deviation storage with stochastic rounding (the TMA
+    # kernel's 16-bit build): one step from the stored state against the oracle; the
+    # GPU output is a deviation from the rest state rounded to FP16 (stochastic: within
+    # one ulp, 2^-10 of the deviation, which is smaller than the population itself),
+    # hence relative 2^-10 of the population plus 1e-6
+    case, fields = W.rayleigh_benard(4096, 2048, seed=6, storage="fp16")
+    case = dict(case, rounding="stochastic")
+    lat = T.Lattice(case, fields)
+    lat.step(3)
+    f0, h0 = lat.populations()
+    lat.step(1)
+    f1, h1 = lat.populations()
+    lat.close()
+    rng = np.random.default_rng(1)
+    xs = np.concatenate([rng.integers(0, 4096, 400), [0, 4095, 127, 128, 0, 4095]])
+    ys = np.concatenate([rng.integers(0, 2048, 400), [0, 0, 2047, 2047, 1, 2046]])
+    o = oracle.Oracle(dict(case, storage="fp32"), None, threads=16)
+    of, oh = o.update_nodes(xs, ys, f0, h0)
+    np.testing.assert_allclose(f1[:, ys, xs].T, of, rtol=2.0**-10, atol=1e-6)
+    np.testing.assert_allclose(h1[:, ys, xs].T, oh, rtol=2.0**-10, atol=1e-6)
+
+
+def test_batched_sweep_full_size_sampled_nodes(T):
+    # the 256-lattice sweep of the batched measurement (FP16 deviations, stochastic
+    # rounding) in one batch with the shape the autotuner keeps there (32-wide strips,
+    # 64 rows): one batch step against the oracle, node by node, on the largest and
+    # smallest lattices
+    cases = W.batched_rb_sweep(count=256, storage="fp16")
+    lats = [T.Lattice(dict(c, rounding="stochastic"), f) for c, f in cases]
+    b = T.Batch(lats)
+    b.set_tile(32, 64, False)
+    b.step(3)
+    order = sorted(range(len(cases)), key=lambda i: cases[i][0]["nx"] * cases[i][0]["ny"])
+    pick = order[:2] + order[-2:]
+    before = {i: lats[i].populations() for i in pick}
+    b.step(1)
+    rng = np.random.default_rng(2)
+    for i in pick:
+        c = cases[i][0]
+        nx, ny = c["nx"], c["ny"]
+        xs = np.concatenate([rng.integers(0, nx, 100), [0, nx - 1, 0, nx - 1]])
+        ys = np.concatenate([rng.integers(0, ny, 100), [0, 0, ny - 1, ny - 1]])
+        f0, h0 = before[i]
+        f1, h1 = lats[i].populations()
+        of, oh = oracle.Oracle(dict(c, storage="fp32"), None, threads=16).update_nodes(xs, ys, f0, h0)
+        np.testing.assert_allclose(f1[:, ys, xs].T, of, rtol=2.0**-10, atol=1e-6)  # FP16, as above
+        np.testing.assert_allclose(h1[:, ys, xs].T, oh, rtol=2.0**-10, atol=1e-6)
+    b.close()
+    for l in lats:
+        l.close()
+
+
 TILE_CASES = [
     ("periodic_corr_partial", *W.random_periodic(150, 45, seed=71, force="accel")),
     ("periodic_tg_force", *W.random_periodic(70, 37, seed=72, force="taylor_green")),
@@ -303,7 +356,7 @@ TILE_CASES = [
 
 @pytest.mark.parametrize("name,case,fields", TILE_CASES, ids=[c[0] for c in TILE_CASES])
 def test_tile_kernel_agrees_with_the_marching_kernel(T, name, case, fields):
-    # one node per thread on 32 x 8 tiles against row marching: the same per-node code;
+    # one node per thread on 32 x 4 tiles against row marching: the same per-node code;
     # wall helpers inlined into another kernel may differ by one ulp (5e-7 absolute)
     states = []
     for kind in (2, 1):

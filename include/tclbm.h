@@ -190,6 +190,13 @@ const char* tclbm_last_error(void);
  * profiling ("tclbm_step_kernel<...> grid (gx, gy) block (bx)"). */
 const char* tclbm_describe(const tclbm_lattice* lat);
 
+/* Test hook for the timeout path (no counterpart in the paper): with row in [0, ny) the
+ * TMA-fed kernel (variant 0) never copies that source row, so the bounded waits on it
+ * expire after 1 s, the kernel records the failure and returns, and the next
+ * synchronising call returns TCLBM_ETIMEOUT (the state is then invalid; re-initialise
+ * it).  row = -1 turns the hook off.  EINVAL for other rows. */
+tclbm_status tclbm_test_skip_row(tclbm_lattice* lat, int32_t row);
+
 /* Launch-shape override for tuning; 0 keeps the library's choice.  Kernel variants 0
  * and 1: strip width tx (32, 64 or 128 nodes) and rows per CTA ty (>= 1).  Variant 2:
  * the tile (tx, ty) = (BX, BY), one of 16x4, 16x8, 32x4, 32x8, 32x16, 64x4, 64x8,

@@ -112,6 +112,7 @@ void derive(tclbm_lattice* L) {
     const tclbm_params& p = L->prm;
     DevParams& d = L->dp;
     memset(&d, 0, sizeof d);
+    d.skip_row = -1;  // the timeout test hook is off
     d.nx = p.nx;
     d.ny = p.ny;
     d.pitch = pitch_of(p.nx);
@@ -687,6 +688,17 @@ tclbm_status tclbm_set_tile(tclbm_lattice* L, int32_t tx, int32_t ty) {
     }
     L->tx = ntx;
     L->ty = nty;
+    return TCLBM_OK;
+}
+
+tclbm_status tclbm_test_skip_row(tclbm_lattice* L, int32_t row) {
+    if (!L) return fail(TCLBM_EINVAL, "lattice is NULL");
+    if (row < -1 || row >= L->prm.ny) return fail(TCLBM_EINVAL, "row must be -1 or in [0, ny)");
+    L->dp.skip_row = row;
+    if (L->graph) {  // a captured graph holds the old parameters
+        cudaGraphExecDestroy(L->graph);
+        L->graph = nullptr;
+    }
     return TCLBM_OK;
 }
 

@@ -52,6 +52,7 @@ struct DevParams {
     int rounding;              // 16-bit stores: 0 nearest, 1 stochastic
     unsigned* step_ctr;        // two step counters, alternated by launch parity
     int parity;                // index of the source copy of this launch
+    int skip_row;              // test hook: the TMA producer never copies this source row (-1: off)
 };
 
 // Counter-based 32-bit mix of (node, pair, step): random bits for stochastic rounding.

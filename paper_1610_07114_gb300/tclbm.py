@@ -95,6 +95,8 @@ _lib.tclbm_describe.argtypes = [_vp]
 _lib.tclbm_describe.restype = ctypes.c_char_p
 _lib.tclbm_set_tile.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
 _lib.tclbm_set_tile.restype = ctypes.c_int
+_lib.tclbm_test_skip_row.argtypes = [_vp, ctypes.c_int32]
+_lib.tclbm_test_skip_row.restype = ctypes.c_int
 _lib.tclbm_set_kernel.argtypes = [_vp, ctypes.c_int32]
 _lib.tclbm_set_kernel.restype = ctypes.c_int
 _lib.tclbm_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, _vp, ctypes.POINTER(_vp)]
@@ -191,6 +193,10 @@ def tclbm_set_tile(h, tx, ty):
 
 def tclbm_set_kernel(h, kind):
     _check(_lib.tclbm_set_kernel(h, int(kind)), "tclbm_set_kernel")
+
+
+def tclbm_test_skip_row(h, row):
+    _check(_lib.tclbm_test_skip_row(h, int(row)), "tclbm_test_skip_row")
 
 
 def tclbm_describe(h) -> str:

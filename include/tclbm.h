@@ -191,7 +191,8 @@ const char* tclbm_last_error(void);
 const char* tclbm_describe(const tclbm_lattice* lat);
 
 /* Test hook for the timeout path (no counterpart in the paper): with row in [0, ny) the
- * TMA-fed kernel (variant 0) never copies that source row, so the bounded waits on it
+ * TMA-fed kernel (variant 0, FP32 storage; other formats ignore the hook) never copies
+ * that source row, so the bounded waits on it
  * expire after 1 s, the kernel records the failure and returns, and the next
  * synchronising call returns TCLBM_ETIMEOUT (the state is then invalid; re-initialise
  * it).  row = -1 turns the hook off.  EINVAL for other rows. */

@@ -74,3 +74,27 @@ def test_non_finite_state_is_reported(T):
         lat.diagnostics()
     assert err.value.status == T.ENONFINITE
     lat.close()
+
+
+@pytest.mark.parametrize("name,make", [
+    ("rb_walls", lambda: W.rayleigh_benard(96, 48, Ra=2e4, seed=11)),
+    ("periodic", lambda: W.random_periodic(70, 37, seed=12, force="accel")),
+    ("x_ends", lambda: W.with_walls(*W.random_periodic(66, 10, seed=13), axis="x", kind="equilibrium")),
+])
+def test_resume_from_populations_equals_an_uninterrupted_run(T, name, make):
+    # checkpoint = the populations read out; resume = a new handle set from them
+    case, fields = make()
+    whole = T.Lattice(case, fields)
+    whole.step(40)
+    f_ref, h_ref = whole.populations()
+    whole.close()
+    first = T.Lattice(case, fields)
+    first.step(17)
+    f, h = first.populations()
+    first.close()
+    second = T.Lattice(case)
+    second.set_populations(f, h)
+    second.step(23)
+    f2, h2 = second.populations()
+    second.close()
+    assert np.array_equal(f2, f_ref) and np.array_equal(h2, h_ref)

@@ -174,6 +174,22 @@ tclbm_status tclbm_snapshot_velocity(tclbm_lattice* lat);
 tclbm_status tclbm_get_populations(tclbm_lattice* lat, double* f, double* h, int32_t on_device);
 tclbm_status tclbm_set_populations(tclbm_lattice* lat, const double* f, const double* h, int32_t on_device);
 
+/* Row exchange of a slab decomposition along y (no counterpart in the paper, which
+ * steps one lattice as a whole).  One lattice cut into slabs of whole rows, each slab a
+ * lattice that also holds `g` rows of its neighbours, stays equal row for row to the
+ * undivided lattice for g/2 steps (a node's update reads the rows next to it and the
+ * correction-term gradient of Section IV reads the velocity one row further); this
+ * call refreshes those rows.  It copies rows [src_row, src_row + rows) of src's
+ * current state into rows [dst_row, dst_row + rows) of dst's, every population plane,
+ * in the storage format as stored (a device-to-device copy; nothing is converted).
+ * Both lattices need the same nx, storage format and thermal flag, and both row ranges
+ * must lie inside their lattices (the same lattice is allowed with disjoint ranges);
+ * EINVAL otherwise.  rows = 0 does nothing.  Asynchronous: queued on dst's stream after
+ * the work already queued on src's stream, and later work on src's stream waits for the
+ * copy.  The copy changes no step count. */
+tclbm_status tclbm_copy_rows(tclbm_lattice* dst, int32_t dst_row, tclbm_lattice* src, int32_t src_row,
+                             int32_t rows);
+
 /* Time steps taken since the last init. */
 int64_t tclbm_steps_done(const tclbm_lattice* lat);
 

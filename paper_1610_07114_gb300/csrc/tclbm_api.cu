@@ -662,6 +662,7 @@ tclbm_status tclbm_destroy(tclbm_lattice* L) {
     dev_free(L, L->usnap, L->usnap_bytes);
     dev_free(L, L->stage, L->stage_bytes);
     dev_free(L, L->err, 256);
+    if (L->copy_event) cudaEventDestroy(L->copy_event);
     delete L;
     return TCLBM_OK;
 }
@@ -911,6 +912,46 @@ tclbm_status tclbm_set_populations(tclbm_lattice* L, const double* f, const doub
     if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
     if (tmp) dev_free(L, tmp, 2 * bytes);
     if (e != cudaSuccess) return cuda_fail(e, "set_populations");
+    return TCLBM_OK;
+}
+
+// Slab decomposition along y: whole rows of every population plane, in the storage
+// format as stored (post-collision values at their own node, ready for the next pull).
+tclbm_status tclbm_copy_rows(tclbm_lattice* dst, int32_t dst_row, tclbm_lattice* src, int32_t src_row,
+                             int32_t rows) {
+    if (!dst || !src) return fail(TCLBM_EINVAL, "lattice is NULL");
+    if (dst->prm.nx != src->prm.nx || dst->storage != src->storage || dst->nplanes != src->nplanes)
+        return fail(TCLBM_EINVAL, "lattices differ in nx, storage format or thermal flag");
+    if (rows < 0 || src_row < 0 || dst_row < 0 || (int64_t)src_row + rows > src->prm.ny ||
+        (int64_t)dst_row + rows > dst->prm.ny)
+        return fail(TCLBM_EINVAL, "rows [%d, %d) of %d and [%d, %d) of %d are not all inside the lattices", src_row,
+                    src_row + rows, src->prm.ny, dst_row, dst_row + rows, dst->prm.ny);
+    if (dst == src && dst_row < src_row + rows && src_row < dst_row + rows)
+        return fail(TCLBM_EINVAL, "source and destination rows overlap");
+    if (rows == 0) return TCLBM_OK;
+    const size_t row_bytes = (size_t)dst->dp.pitch * dst->elem;
+    const size_t width = (size_t)rows * row_bytes;
+    const size_t dplane = (size_t)dst->dp.plane * dst->elem, splane = (size_t)src->dp.plane * src->elem;
+    char* d = (char*)dst->buf[dst->cur] + (size_t)dst_row * row_bytes;
+    const char* s = (const char*)src->buf[src->cur] + (size_t)src_row * row_bytes;
+    const bool cross = dst->stream != src->stream;
+    if (cross) {  // the copy follows work queued on the source's stream
+        if (!src->copy_event) CK(cudaEventCreateWithFlags(&src->copy_event, cudaEventDisableTiming));
+        if (!dst->copy_event) CK(cudaEventCreateWithFlags(&dst->copy_event, cudaEventDisableTiming));
+        CK(cudaEventRecord(src->copy_event, src->stream));
+        CK(cudaStreamWaitEvent(dst->stream, src->copy_event, 0));
+    }
+    if (dplane <= (size_t)INT32_MAX && splane <= (size_t)INT32_MAX) {
+        CK(cudaMemcpy2DAsync(d, dplane, s, splane, width, (size_t)dst->nplanes, cudaMemcpyDeviceToDevice,
+                             dst->stream));
+    } else {
+        for (int q = 0; q < dst->nplanes; ++q)
+            CK(cudaMemcpyAsync(d + q * dplane, s + q * splane, width, cudaMemcpyDeviceToDevice, dst->stream));
+    }
+    if (cross) {  // and the source's later steps, which overwrite these rows, follow the copy
+        CK(cudaEventRecord(dst->copy_event, dst->stream));
+        CK(cudaStreamWaitEvent(src->stream, dst->copy_event, 0));
+    }
     return TCLBM_OK;
 }
 

@@ -48,6 +48,8 @@ struct tclbm_lattice {
     // CUDA graph of 2 * kGraphPairs step launches (parity preserved)
     cudaGraphExec_t graph = nullptr;
     int graph_tx = 0, graph_ty = 0, graph_kernel = -1;
+    // orders row copies between lattices on different streams (created on first use)
+    cudaEvent_t copy_event = nullptr;
 };
 
 namespace tclbm {

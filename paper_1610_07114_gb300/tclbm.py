@@ -99,6 +99,8 @@ _lib.tclbm_test_skip_row.argtypes = [_vp, ctypes.c_int32]
 _lib.tclbm_test_skip_row.restype = ctypes.c_int
 _lib.tclbm_set_kernel.argtypes = [_vp, ctypes.c_int32]
 _lib.tclbm_set_kernel.restype = ctypes.c_int
+_lib.tclbm_copy_rows.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.c_int32, ctypes.c_int32]
+_lib.tclbm_copy_rows.restype = ctypes.c_int
 _lib.tclbm_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, _vp, ctypes.POINTER(_vp)]
 _lib.tclbm_batch_create.restype = ctypes.c_int
 _lib.tclbm_batch_set_lattices.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int32]
@@ -197,6 +199,10 @@ def tclbm_set_kernel(h, kind):
 
 def tclbm_test_skip_row(h, row):
     _check(_lib.tclbm_test_skip_row(h, int(row)), "tclbm_test_skip_row")
+
+
+def tclbm_copy_rows(dst, dst_row, src, src_row, rows):
+    _check(_lib.tclbm_copy_rows(dst, dst_row, src, src_row, rows), "tclbm_copy_rows")
 
 
 def tclbm_describe(h) -> str:

@@ -424,12 +424,16 @@ def bench_gpu(args):
     if not args.no_probe:
         from paper_1610_07114_gb300 import workloads as W
 
-        for storage in args.probe_storages:
-            pc, pf = W.rayleigh_benard(args.probe_nx, args.probe_ny, Ra=1e4, seed=2, storage=storage)
+        sizes = [(args.probe_nx, args.probe_ny)]
+        if not args.no_probe_large:
+            sizes.append((2 * args.probe_nx, 2 * args.probe_ny))
+        for (pnx, pny), storage in [(sz, st) for sz in sizes for st in args.probe_storages]:
+            pc, pf = W.rayleigh_benard(pnx, pny, Ra=1e4, seed=2, storage=storage)
             pl = tclbm.Lattice(pc, pf, stream=stream.cuda_stream)
             pl.step(4)
             torch.cuda.synchronize()
-            reps = args.probe_steps
+            # the same bytes per probe at every size (at least 20 launches)
+            reps = max(20, args.probe_steps * args.probe_nx * args.probe_ny // (pnx * pny))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             pl.step(reps)
@@ -438,8 +442,8 @@ def bench_gpu(args):
             dt = e0.elapsed_time(e1) / 1e3 / reps
             pn = pc["nx"] * pc["ny"]
             achieved = BYTES_PER_LU[storage] * pn / dt / 1e9
-            key = f"rb_{args.probe_nx}x{args.probe_ny}_{storage}"
-            probes.append({"workload": key, "kernel": pl.describe(), "LU_per_s": pn / dt,
+            key = f"rb_{pnx}x{pny}_{storage}"
+            probes.append({"workload": key, "kernel": pl.describe(), "LU_per_s": pn / dt, "launches": reps,
                            "us_per_launch": dt * 1e6, "achieved_GBs": achieved, "peak_GBs": peak,
                            "frac": achieved / peak, "bytes_per_LU": BYTES_PER_LU[storage],
                            "traffic": _profiled_traffic(key)})
@@ -512,6 +516,8 @@ def main():
     ap.add_argument("--probe-steps", type=int, default=200)
     ap.add_argument("--probe-storages", nargs="*", default=["fp32", "bf16", "fp16"])
     ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--no-probe-large", action="store_true",
+                    help="skip the second probe size (2 probe-nx x 2 probe-ny)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--profile-run", action="store_true",

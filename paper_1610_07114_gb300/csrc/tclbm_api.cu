@@ -168,10 +168,10 @@ void derive(tclbm_lattice* L) {
     }
 }
 
-// Lattices that fit in L2 are latency-bound: the direct-load kernel with short strips
-// and one or a few rows per CTA exposes the most parallelism.  Larger lattices stream
-// rows through the TMA ring with 128-wide strips of 16 rows (measured best at
-// 4096 x 2048).
+// Lattices that fit in L2 are latency-bound: 2-D tiles of one node per thread (or the
+// direct-load kernel with short strips where tiles do not apply) expose the most
+// parallelism.  Larger lattices stream rows through the TMA ring with 128-wide strips
+// of 16 or 32 rows per CTA (default_shape).
 constexpr long long kSmallNodes = 1LL << 21;
 
 // Launch shape a kernel variant gets by default: (tx, rows per CTA) for the marching
@@ -186,8 +186,14 @@ void default_shape(const tclbm_params& p, int kernel, int& tx, int& ty) {
         long long t = (long long)p.ny * strips / (8LL * 152);
         ty = (int)(t < 2 ? 2 : (t > 16 ? 16 : t));
     } else {
+        // 16 rows per CTA, or 32 where that grid still spans >= 8 waves of resident CTAs
+        // (3 per SM for FP32, 4 for 16-bit): fewer halo rows per node, and the last
+        // wave's tail weighs little (measured: 16 best at 4096 x 2048, 32 faster by
+        // 3-4 % at 8192 x 4096)
         tx = p.nx >= 512 ? 128 : (p.nx >= 96 ? 64 : 32);
-        ty = 16;
+        const long long strips = (p.nx + tx - 1) / tx;
+        const long long resident = 152LL * (p.storage == TCLBM_STORE_FP32 ? 3 : 4);
+        ty = strips * ((p.ny + 31) / 32) >= 8 * resident ? 32 : 16;
     }
 }
 

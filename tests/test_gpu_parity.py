@@ -190,6 +190,22 @@ def test_launch_shapes_are_bit_identical(T):
         assert np.array_equal(f, states[0][0]) and np.array_equal(h, states[0][1])
 
 
+def test_tma_rows_per_cta_are_bit_identical(T):
+    # the TMA kernel's row segments (16 rows by default, 32 on lattices of >= 8 waves)
+    # change which CTA computes a node, not its arithmetic
+    case, fields = W.rayleigh_benard(512, 256, seed=5)
+    states = []
+    for ty in (16, 32, 7, 48):
+        lat = T.Lattice(case, fields)
+        lat.set_kernel(0)
+        lat.set_tile(128, ty)
+        lat.step(21)
+        states.append(lat.populations())
+        lat.close()
+    for f, h in states[1:]:
+        assert np.array_equal(f, states[0][0]) and np.array_equal(h, states[0][1])
+
+
 KERNEL_CASES = [
     ("periodic_corr", *W.random_periodic(150, 45, seed=21, force="accel")),
     ("periodic_tg_nocorr", *W.random_periodic(97, 33, seed=22, force="taylor_green", correction=False)),

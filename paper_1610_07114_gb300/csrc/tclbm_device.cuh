@@ -258,6 +258,48 @@ __device__ __forceinline__ void dheq(const DevParams& p, float rho, float drho, 
     o[8] = -qb;
 }
 
+// Lane pairs.  Blackwell issues two FP32 lanes per FADD2 / FMUL2 / FFMA2, each lane
+// rounded like __fadd_rn / __fmul_rn / __fmaf_rn.  The collision keeps populations in
+// the pairs (1,2), (3,4), (5,6), (7,8) from the raw moments to the store.
+__device__ __forceinline__ float2 pr(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc(-1.0f), a); }  // b * -1 is exact
+
+// Eq. 3 in lane pairs: o0 and P[k] = (o_{2k+1}, o_{2k+2}); m1 = (M10, M01), m3 = (M21, M12).
+__device__ __forceinline__ void eq3_pairs(float rho, float m00, float2 m1, float E, float N, float Pi, float2 m3,
+                                          float M22, float& o0, float2* P) {
+    const float hr = 0.5f * rho, qr = 0.25f * rho;
+    o0 = rho * (m00 - E + M22);
+    const float2 e = fma2(bc(N), pr(0.5f, -0.5f), bc(0.5f * E));  // ((E + N) / 2, (E - N) / 2)
+    const float2 c = sub2(e, bc(M22));
+    const float2 mm = sub2(m1, pr(m3.y, m3.x));  // (M10 - M12, M01 - M21)
+    P[0] = mul2(bc(hr), add2(c, mm));
+    P[1] = mul2(bc(hr), sub2(c, mm));
+    const float2 sd = fma2(bc(m3.y), pr(1.0f, -1.0f), bc(m3.x));  // (M21 + M12, M21 - M12)
+    const float2 pm = fma2(bc(Pi), pr(1.0f, -1.0f), bc(M22));   // (M22 + Pi, M22 - Pi)
+    P[2] = mul2(bc(qr), add2(pm, sd));
+    P[3] = mul2(bc(qr), sub2(pm, sd));
+}
+
+// dheq in lane pairs: o0 and P[k] = (o_{2k+1}, o_{2k+2}); u = (ux, uy), u2 = (ux^2, uy^2).
+__device__ __forceinline__ void dheq_pairs(const DevParams& p, float rho, float drho, float2 u, float2 u2, float RT,
+                                           float dRT, float Et, float dEt, float& o0, float2* P) {
+    const float uu = u2.x + u2.y;
+    const float A = Et + RT, B = Et + 2.0f * RT;
+    const float dC = dRT * A + p.RT0 * (dEt + dRT);
+    const float hr = 0.5f * rho, qb = 0.25f * rho * B * u.x * u.y;
+    o0 = drho * p.hbase[0] + rho * (dEt - B * uu - 2.0f * dC);
+    const float2 axis = bc(drho * p.hbase[1] + hr * dC);
+    const float2 bu2 = mul2(bc(B), u2);
+    P[0] = fma2(bc(hr), fma2(bc(A), u, bu2), axis);
+    P[1] = fma2(bc(hr), fma2(bc(-A), u, bu2), axis);
+    P[2] = pr(qb, -qb);
+    P[3] = pr(qb, -qb);
+}
+
 // Source populations S_a (Section III raw moments) at the given state.
 __device__ __forceinline__ void source(float rho, float ux, float uy, float ax, float ay, float* o) {
     eq3(rho, 0.0f, ax, ay, 2.0f * (ax * ux + ay * uy), 2.0f * (ax * ux - ay * uy), ax * uy + ay * ux,
@@ -284,88 +326,110 @@ __device__ __forceinline__ void collide(const DevParams& p, const float* f, cons
     const float rho = m.rho, drho = m.drho, ux = m.ux, uy = m.uy, ax = m.ax, ay = m.ay;
     const float irho = m.irho;
     const float RT0 = p.RT0, RT = m.RT, dRT = m.dRT;
-    const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy, uu = ux2 + uy2;
+    const float2 u = pr(ux, uy), a = pr(ax, ay);
+    const float2 u2 = mul2(u, u);
+    const float ux2 = u2.x, uy2 = u2.y, uxy = ux * uy, uu = ux2 + uy2;
     const float mup = mu_over_p(p, irho, RT);
     const float w1 = p.visc_law == VISC_W1 ? p.visc : rcp(mup + 0.5f);
     const float w2 = p.bgk ? w1 : p.w2, w3 = p.bgk ? w1 : p.w3, w4 = p.bgk ? w1 : p.w4;
 
-    // raw moments (Eq. 1) of the deviations; the rest state contributes 1, RT0, RT0^2
-    const float S20 = (f[1] + f[3]) + (f[5] + f[6]) + (f[7] + f[8]);
-    const float S02 = (f[2] + f[4]) + (f[5] + f[6]) + (f[7] + f[8]);
-    const float S11 = (f[5] - f[6]) + (f[7] - f[8]);
-    const float S21 = (f[5] + f[6]) - (f[7] + f[8]);
-    const float S12 = (f[5] - f[6]) - (f[7] - f[8]);
-    const float S22 = (f[5] + f[6]) + (f[7] + f[8]);
-    const float dr20 = (S20 - RT0 * drho) * irho;  // r20 - RT0
-    const float dr02 = (S02 - RT0 * drho) * irho;
+    // raw moments (Eq. 1) of the deviations; the rest state contributes 1, RT0, RT0^2.
+    // Pairs hold (x, y) mirror images: (r20, r02), (r10, r01), (k21, k12), (M21, M12); usw = (uy, ux).
+    const float2 s13 = add2(pr(f[1], f[2]), pr(f[3], f[4]));  // (f1 + f3, f2 + f4)
+    const float2 a57 = add2(pr(f[5], f[6]), pr(f[7], f[8]));  // (f5 + f7, f6 + f8)
+    const float2 d57 = sub2(pr(f[5], f[6]), pr(f[7], f[8]));  // (f5 - f7, f6 - f8)
+    const float S22 = a57.x + a57.y, S11 = a57.x - a57.y;
+    const float2 dr2 = mul2(fma2(bc(drho), bc(-RT0), add2(s13, bc(S22))), bc(irho));  // (r20, r02) - RT0
     const float dr22 = (S22 - RT0 * RT0 * drho) * irho;  // r22 - RT0^2
-    const float r11 = S11 * irho, r21 = S21 * irho, r12 = S12 * irho;
-    const float r20 = RT0 + dr20, r02 = RT0 + dr02;
-    const float r10 = ux - 0.5f * ax, r01 = uy - 0.5f * ay;
+    const float r11 = S11 * irho;
+    const float2 r3 = mul2(fma2(bc(d57.y), pr(1.0f, -1.0f), bc(d57.x)), bc(irho));  // (r21, r12)
+    const float2 r2 = add2(dr2, bc(RT0));
+    const float2 r1 = fma2(bc(-0.5f), a, u);  // (r10, r01)
+    const float2 usw = pr(uy, ux), r1sw = pr(r1.y, r1.x);
+    const float2 m2u = mul2(bc(-2.0f), u);
 
     // central moments about u by the binomial theorem (Eq. 4), k20, k02 less RT0, k22 less RT0^2
-    const float dk20 = dr20 - 2.0f * ux * r10 + ux2;
-    const float dk02 = dr02 - 2.0f * uy * r01 + uy2;
-    const float k11 = r11 - ux * r01 - uy * r10 + uxy;
-    const float k21 = r21 - 2.0f * ux * r11 - uy * r20 + ux2 * r01 + 2.0f * uxy * r10 - ux2 * uy;
-    const float k12 = r12 - 2.0f * uy * r11 - ux * r02 + uy2 * r10 + 2.0f * uxy * r01 - ux * uy2;
-    const float dk22 = dr22 - 2.0f * ux * r12 - 2.0f * uy * r21 + ux2 * r02 + uy2 * r20 + 4.0f * uxy * r11
-                     - 2.0f * ux * uy2 * r10 - 2.0f * ux2 * uy * r01 + ux2 * uy2;
+    const float2 dk2 = fma2(m2u, r1, add2(dr2, u2));  // (k20, k02) - RT0
+    const float k11 = r11 - ux * r1.y - uy * r1.x + uxy;
+    // k21 = r21 - 2 ux r11 - uy (r20 + ux^2) + ux^2 r01 + 2 ux uy r10, and its mirror k12
+    const float2 k3 = fma2(bc(2.0f * uxy), r1,
+                           fma2(u2, r1sw, fma2(mul2(bc(-1.0f), usw), add2(r2, u2), fma2(m2u, bc(r11), r3))));
+    // k22 = r22 - 2 (ux r12 + uy r21) + ux^2 r02 + uy^2 r20 + 4 ux uy r11 - 2 ux uy (uy r10 + ux r01) + ux^2 uy^2
+    const float2 v22 = fma2(mul2(bc(-2.0f), usw), r3, mul2(pr(uy2, ux2), r2));
+    const float2 w22 = mul2(usw, r1);
+    const float dk22 = dr22 + (v22.x + v22.y) + uxy * (4.0f * r11 - 2.0f * (w22.x + w22.y) + uxy);
 
     // Eq. 8 towards the equilibria of f_bar shifted by the correction term
     // (E~eq = 2RT - (dx+dy)/2, N~eq = (dy-dx)/2, M~22eq = RT^2; E, M22 kept less 2RT0, RT0^2)
     const float dRT2 = dRT * (2.0f * RT0 + dRT);  // RT^2 - RT0^2
     const float Pis = (1.0f - w1) * k11;
-    const float Ns = w1 * (0.5f * (dy - dx)) + (1.0f - w1) * (dk20 - dk02);
-    const float dEs = w2 * (2.0f * dRT - 0.5f * (dx + dy)) + (1.0f - w2) * (dk20 + dk02);
-    const float M21s = (1.0f - w3) * k21;
-    const float M12s = (1.0f - w3) * k12;
+    const float Ns = w1 * (0.5f * (dy - dx)) + (1.0f - w1) * (dk2.x - dk2.y);
+    const float dEs = w2 * (2.0f * dRT - 0.5f * (dx + dy)) + (1.0f - w2) * (dk2.x + dk2.y);
+    const float2 m3s = mul2(bc(1.0f - w3), k3);  // (M21*, M12*) central
     const float dM22s = w4 * dRT2 + (1.0f - w4) * dk22;
 
-    // Eq. 18: raw post-collision moments of f_bar^*
-    const float Pi = Pis + uxy - 0.5f * (ax * uy + ay * ux);
-    const float N = Ns + ux2 - uy2 - (ax * ux - ay * uy);
-    const float dE = dEs + uu - (ax * ux + ay * uy);
-    const float E = 2.0f * RT0 + dE;
-    const float M21 = M21s + 2.0f * ux * Pi + 0.5f * uy * (E + N) - 2.0f * ux2 * uy + 0.5f * ay * ux2 + ax * uxy;
-    const float M12 = M12s + 2.0f * uy * Pi + 0.5f * ux * (E - N) - 2.0f * uy2 * ux + 0.5f * ax * uy2 + ay * uxy;
-    const float dM22 = dM22s + 2.0f * ux * M12 + 2.0f * uy * M21 - 0.5f * uu * E + 0.5f * (ux2 - uy2) * N
-                     - 4.0f * uxy * Pi + 3.0f * ux2 * uy2 - ax * ux * uy2 - ay * uy * ux2;
-
     // raw moments of S (Section III) and of C (Section IV)
-    const float Es_ = 2.0f * (ax * ux + ay * uy), Ns_ = 2.0f * (ax * ux - ay * uy), Pis_ = ax * uy + ay * ux;
-    const float M21s_ = ay * ux2 + 2.0f * ax * uxy, M12s_ = ax * uy2 + 2.0f * ay * uxy;
-    const float M22s_ = 2.0f * ax * ux * uy2 + 2.0f * ay * uy * ux2;
-    const float Ec = dx + dy, Nc = dx - dy, M21c = uy * dx, M12c = ux * dy;
+    const float2 au = mul2(a, u);  // (ax ux, ay uy)
+    const float Es_ = 2.0f * (au.x + au.y), Ns_ = 2.0f * (au.x - au.y), Pis_ = ax * uy + ay * ux;
+    const float2 m3s_ = fma2(pr(ay, ax), u2, mul2(bc(2.0f * uxy), a));  // (ay ux^2 + 2 ax ux uy, mirror)
+    const float M22s_ = 2.0f * uxy * Pis_;
+    const float Ec = dx + dy, Nc = dx - dy;
+    const float2 m3c = mul2(usw, pr(dx, dy));  // (uy dx, ux dy)
+    const float2 m3sc = add2(m3s_, m3c);
 
-    // Eq. 27: f_out = f_bar^* + S + C.  Eq. 3 is linear and gives the rest state from
-    // (1, 0, 0, 2RT0, 0, 0, 0, 0, RT0^2), so f_out - f_rest = rho Eq3(deviation moments)
-    // + (rho - 1) f_rest.
-    eq3(rho, 0.0f, ux + 0.5f * ax, uy + 0.5f * ay, dE + Es_ + Ec, N + Ns_ + Nc, Pi + Pis_, M21 + M21s_ + M21c,
-        M12 + M12s_ + M12c, dM22 + M22s_, fo);
+    // Eq. 18: raw post-collision moments of f_bar^*
+    const float Pi = Pis + uxy - 0.5f * Pis_;
+    const float N = Ns + ux2 - uy2 - (au.x - au.y);
+    const float dE = dEs + uu - (au.x + au.y);
+    const float E = 2.0f * RT0 + dE;
+    // M21 = M21* + 2 ux Pi + uy (E + N) / 2 - 2 ux^2 uy + ay ux^2 / 2 + ax ux uy, and its mirror
+    const float2 en = fma2(bc(N), pr(1.0f, -1.0f), bc(E));  // (E + N, E - N)
+    const float2 m3 = fma2(a, bc(uxy),
+                           fma2(mul2(bc(0.5f), pr(ay, ax)), u2,
+                                fma2(mul2(bc(-2.0f), u2), usw,
+                                     fma2(mul2(bc(0.5f), usw), en, fma2(bc(2.0f * Pi), u, m3s)))));
+    const float2 w3m = mul2(usw, m3);  // (uy M21, ux M12)
+    const float dM22 = dM22s + 2.0f * (w3m.x + w3m.y) - 0.5f * uu * E + 0.5f * (ux2 - uy2) * N - 4.0f * uxy * Pi
+                     + 3.0f * ux2 * uy2 - uxy * Pis_;
+
+    float2 FO[4];
+    eq3_pairs(rho, 0.0f, fma2(bc(0.5f), a, u), dE + Es_ + Ec, N + Ns_ + Nc, Pi + Pis_, add2(m3, m3sc),
+              dM22 + M22s_, fo[0], FO);
+    fo[0] += drho * p.fbase[0];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) fo[q] += drho * p.fbase[q];
+    for (int k = 0; k < 4; ++k) {
+        const float2 r = fma2(bc(drho), pr(p.fbase[2 * k + 1], p.fbase[2 * k + 2]), FO[k]);
+        fo[2 * k + 1] = r.x;
+        fo[2 * k + 2] = r.y;
+    }
 
     if (THERMAL) {
         // g = f_bar + S/2 + C/2 - f^eq through its moments (M00, M10, M01 of g vanish)
-        const float dEg = dr20 + dr02 + 0.5f * (Es_ + Ec) - 2.0f * dRT - uu;
-        const float dNg = (dr20 - dr02) + 0.5f * (Ns_ + Nc) - (ux2 - uy2);
+        const float dEg = dr2.x + dr2.y + 0.5f * (Es_ + Ec) - 2.0f * dRT - uu;
+        const float dNg = (dr2.x - dr2.y) + 0.5f * (Ns_ + Nc) - (ux2 - uy2);
         const float dPig = r11 + 0.5f * Pis_ - uxy;
-        const float dM21g = r21 + 0.5f * (M21s_ + M21c) - uy * (RT + ux2);
-        const float dM12g = r12 + 0.5f * (M12s_ + M12c) - ux * (RT + uy2);
+        // (M21, M12) of g: r21 + (M21 of S + C) / 2 - uy (RT + ux^2), and its mirror
+        const float2 m3g = fma2(mul2(bc(-1.0f), usw), add2(bc(RT), u2), fma2(bc(0.5f), m3sc, r3));
         const float dM22g = dr22 + 0.5f * M22s_ - (dRT2 + RT * uu + ux2 * uy2);
-        float g[9];
-        eq3(rho, 0.0f, 0.0f, 0.0f, dEg, dNg, dPig, dM21g, dM12g, dM22g, g);
+        float g0, he0;
+        float2 G[4], HE[4];
+        eq3_pairs(rho, 0.0f, bc(0.0f), dEg, dNg, dPig, m3g, dM22g, g0, G);
         // 1/w_h = (1/w1 - 1/2)/Pr + 1/2 (lambda = mu c_p / Pr); 1/tau_hf = (Pr - 1) w1
         const float wh = rcp(mup * p.inv_Pr + 0.5f);
         const float kc = p.Pr_m1 * w1 * (1.0f - 0.5f * wh);
-        float he[9];
-        dheq(p, rho, drho, ux, uy, RT, dRT, m.Et, m.dEt, he);
+        dheq_pairs(p, rho, drho, u, u2, RT, dRT, m.Et, m.dEt, he0, HE);
+        // Z_a = e_a . u - |u|^2 / 2, in the lane pairs
         const float hu = 0.5f * uu;
-        const float Z[9] = {-hu, ux - hu, uy - hu, -ux - hu, -uy - hu, ux + uy - hu, -ux + uy - hu, -ux - uy - hu,
-                            ux - uy - hu};
+        const float2 Z[4] = {sub2(u, bc(hu)), fma2(u, bc(-1.0f), bc(-hu)), fma2(bc(ux), pr(1.0f, -1.0f), bc(uy - hu)),
+                             fma2(bc(ux), pr(-1.0f, 1.0f), bc(-uy - hu))};
+        ho[0] = h[0] - wh * (h[0] - he0) - kc * hu * g0;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) ho[q] = h[q] - wh * (h[q] - he[q]) + kc * Z[q] * g[q];
+        for (int k = 0; k < 4; ++k) {
+            const float2 hp = pr(h[2 * k + 1], h[2 * k + 2]);
+            const float2 r = fma2(mul2(bc(kc), Z[k]), G[k], fma2(bc(-wh), sub2(hp, HE[k]), hp));
+            ho[2 * k + 1] = r.x;
+            ho[2 * k + 2] = r.y;
+        }
     }
 }
 

@@ -123,7 +123,12 @@ def test_shock_tube_plateau_per_format(T, storage, rounding):
     cs = math.sqrt(1.4 * R)
     sel = (np.abs(xt) > 0.2 * cs) & (np.abs(xt) < 0.8 * cs)
     u_plateau = float(np.mean(m["ux"][0][sel]))
-    assert u_plateau == pytest.approx(us, rel={"fp32": 2e-5, "fp16": 2e-4, "bf16": 3e-3}[storage])
+    # Stochastic rounding makes the plateau one draw of the rounding noise; any change in
+    # the FP32 arithmetic draws another.  Its u field is 4.5e-4 (relative L2) off the FP64
+    # oracle, and the 174 plateau nodes share that noise over the acoustic scale, so
+    # their mean is held to that level, not to the deterministic round-to-nearest bound.
+    rel = {"fp32": 2e-5, "fp16": 2e-4 if rounding == "nearest" else 5e-4, "bf16": 3e-3}[storage]
+    assert u_plateau == pytest.approx(us, rel=rel)
 
 
 def _golden_nusselt():

@@ -25,10 +25,14 @@ def test_clock_summary_without_samples_says_so():
     assert s["sm_mhz"] is None and s["reasons"] == ["unsampled"]
 
 
-def test_peak_is_the_measured_copy_bandwidth():
+def test_peak_is_the_measured_copy_bandwidth_else_the_fallback():
     peak, kind = bench._peaks()
-    with open(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")) as fh:
-        assert kind == "measured" and peak == float(json.load(fh)["hbm_gbs"])
+    path = os.path.join(bench.ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            assert kind == "measured" and peak == float(json.load(fh)["hbm_gbs"])
+    else:
+        assert (peak, kind) == (6800.0, "fallback")
 
 
 def test_profiled_traffic_only_for_the_sources_it_was_captured_on(monkeypatch):

@@ -162,7 +162,9 @@ tclbm_status tclbm_diagnostics(tclbm_lattice* lat, double out[TCLBM_NDIAG]);
  * device that loads the library; no cudaMalloc, cudaFree or other allocating call is
  * made.  Lattices above 67,108,864 nodes are rejected with TCLBM_EINVAL.  The first call
  * on a device resolves the array's address with that device current; make it before
- * any stream capture.  All calls share the array: calls that overlap on the GPU race. */
+ * any stream capture.  All calls share the array: calls that overlap on the GPU race.
+ * With host output a non-finite sum returns TCLBM_ENONFINITE, as tclbm_diagnostics()
+ * does; with device output the sums are not inspected (the call does not synchronise). */
 tclbm_status tclbm_diagnostics_noalloc(const tclbm_params* params, const double* f, const double* h,
                                        const double* u_snap, double* out, int32_t out_on_device, void* stream);
 
@@ -213,6 +215,13 @@ const char* tclbm_describe(const tclbm_lattice* lat);
  * synchronising call returns TCLBM_ETIMEOUT (the state is then invalid; re-initialise
  * it).  row = -1 turns the hook off.  EINVAL for other rows. */
 tclbm_status tclbm_test_skip_row(tclbm_lattice* lat, int32_t row);
+
+/* Test hook for the collision's reciprocal (no counterpart in the paper): y[i] = the
+ * reciprocal the step kernels take of R T, mu/p + 1/2 and mu/(p Pr) + 1/2 (the hardware
+ * approximation refined by one Newton step), for n floats at device pointers x, y.
+ * Queued on `stream` (a cudaStream_t, NULL = legacy default), which it synchronises.
+ * EINVAL on n < 0 or NULL arrays with n > 0. */
+tclbm_status tclbm_test_rcp(const float* x, float* y, int64_t n, void* stream);
 
 /* Launch-shape override for tuning; 0 keeps the library's choice.  Kernel variants 0
  * and 1: strip width tx (32, 64 or 128 nodes) and rows per CTA ty (>= 1).  Variant 2:

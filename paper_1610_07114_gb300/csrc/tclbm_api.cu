@@ -156,7 +156,12 @@ void derive(tclbm_lattice* L) {
         d.wall_ux[s] = (float)p.wall[s].ux;
         d.wall_uy[s] = (float)p.wall[s].uy;
         d.wall_T[s] = (float)p.wall[s].T;
+        d.wall_RT[s] = (float)(p.R * p.wall[s].T);
+        d.wall_dRT[s] = (float)(p.R * p.wall[s].T - RTb);
     }
+    d.dRTp = (float)(p.R * p.T0 - RTb);
+    d.inv_bR2 = 2.0 / (b * p.R);  // the same FP64 expression tclbm_diagnostics_noalloc() takes
+    d.T0d = p.T0;
     // rest-state populations f^eq(1, 0, RT0), h^eq(1, 0, RT0) with Et = Et0
     const double x0 = 1.0 - RTb, x1 = 0.5 * RTb;
     const double fr[9] = {x0 * x0, x1 * x0, x0 * x1, x1 * x0, x0 * x1, x1 * x1, x1 * x1, x1 * x1, x1 * x1};
@@ -345,9 +350,9 @@ __device__ __forceinline__ void node_fields(const DevParams& p, const ST* __rest
     sh = 0;
     if (THERMAL) {
         for (int q = 0; q < 9; ++q) sh += (double)p.hbase[q] + hv[q];
-        T = 2.0 / ((double)p.b * (double)p.R) * (sh / r - 0.5 * (vx * vx + vy * vy));
+        T = p.inv_bR2 * (sh / r - 0.5 * (vx * vx + vy * vy));
     } else {
-        T = p.T0;
+        T = p.T0d;
     }
 }
 
@@ -706,6 +711,24 @@ tclbm_status tclbm_test_skip_row(tclbm_lattice* L, int32_t row) {
         cudaGraphExecDestroy(L->graph);
         L->graph = nullptr;
     }
+    return TCLBM_OK;
+}
+
+namespace {
+// The reciprocal the collision takes of R T, mu/p + 1/2 and the thermal rate's argument.
+__global__ void rcp_kernel(const float* __restrict__ x, float* __restrict__ y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = tclbm::rcp(x[i]);
+}
+}  // namespace
+
+tclbm_status tclbm_test_rcp(const float* x, float* y, int64_t n, void* stream) {
+    if (n < 0 || (n > 0 && (!x || !y))) return fail(TCLBM_EINVAL, "x, y must be device arrays of n >= 0 floats");
+    if (n == 0) return TCLBM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    rcp_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, y, n);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
     return TCLBM_OK;
 }
 

@@ -48,11 +48,18 @@ struct DevParams {
     const float* cy;
     int wall_kind[4], wall_therm[4];
     float wall_rho[4], wall_ux[4], wall_uy[4], wall_T[4];
+    // R T of each wall and its deviation R T - RT0, both formed in FP64 on the host: an
+    // FP32 product R T (R = 1/6 is not a float) would shift the wall temperature by 3e-8
+    float wall_RT[4], wall_dRT[4];
+    float dRTp;  // R T0 - RT0, formed in FP64 (athermal lattices)
     float fbase[9], hbase[9];  // rest-state populations f^eq(1, 0, T0), h^eq(1, 0, T0)
     int rounding;              // 16-bit stores: 0 nearest, 1 stochastic
     unsigned* step_ctr;        // two step counters, alternated by launch parity
     int parity;                // index of the source copy of this launch
     int skip_row;              // test hook: the TMA producer never copies this source row (-1: off)
+    // FP64 constants of the field conversions (moments, diagnostics): T = inv_bR2 (E - u^2/2)
+    // with inv_bR2 = 2 / (b R), and T0, as the FP64 initialisation uses them
+    double inv_bR2, T0d;
 };
 
 // Counter-based 32-bit mix of (node, pair, step): random bits for stochastic rounding.
@@ -184,7 +191,7 @@ __device__ __forceinline__ Macro macro_of(const DevParams& p, const float* f, co
         m.RT = __fadd_rn(p.RT0, m.dRT);
     } else {
         m.RT = p.RTp;
-        m.dRT = __fsub_rn(p.RTp, p.RT0);
+        m.dRT = p.dRTp;
         m.dEt = 0.0f;
         m.Et = p.Et0;
     }
@@ -459,31 +466,37 @@ struct SideIdx<SIDE_XP> {
 // wall density and both momentum components of Eq. 20 imposed, normal unknown closed by
 // bounce-back of its non-equilibrium part.  Works on deviations directly: the scheme is
 // linear and opposite directions have equal rest weights, whose known/incoming sums
-// (f_rest over K plus twice over I) add up to exactly 1.
+// (f_rest over K plus twice over I) add up to exactly 1.  The wall density is carried as
+// 1 + drho_w: an O(1) FP32 rho_w would round away the low bits of the density deviation,
+// and rho_w u_w would then force the moving wall by ~1e-9 every step.
 template <int SIDE>
 __device__ __forceinline__ void zouhe(const DevParams& p, int x, int y, float* f) {
     using S = SideIdx<SIDE>;
     const float dsum = (f[0] + f[S::it] + f[S::imt]) + 2.0f * (f[S::on] + f[S::op] + f[S::om]);
-    float rho_w, an, at;
+    float drho_w, an, at;
     if (p.force_kind == FORCE_TAYLOR_GREEN) {
         float Fx, Fy;
         force_at(p, x, y, 0.0f, Fx, Fy);
         const float Fn = Fx * S::nxv + Fy * S::nyv, Ft = Fx * S::txv + Fy * S::tyv;
-        rho_w = 1.0f + (dsum - 0.5f * Fn);
-        an = Fn / rho_w;
-        at = Ft / rho_w;
+        drho_w = dsum - 0.5f * Fn;
+        const float irw = 1.0f / (1.0f + drho_w);
+        an = Fn * irw;
+        at = Ft * irw;
     } else {
         an = (p.force_kind == FORCE_ACCEL) ? (p.ax * S::nxv + p.ay * S::nyv) : 0.0f;
         at = (p.force_kind == FORCE_ACCEL) ? (p.ax * S::txv + p.ay * S::tyv) : 0.0f;
-        rho_w = (1.0f + dsum) / (1.0f + 0.5f * an);
+        // rho_w = (1 + dsum) / (1 + an / 2), i.e. drho_w = (dsum - an / 2) / (1 + an / 2)
+        drho_w = (dsum - 0.5f * an) / (1.0f + 0.5f * an);
     }
+    const float rho_w = 1.0f + drho_w;
     const float Fn = rho_w * an, Ft = rho_w * at;
     const float uwt = p.wall_ux[SIDE] * S::txv + p.wall_uy[SIDE] * S::tyv;
     const float dn = -0.5f * rho_w * an * (1.0f - uwt * uwt);
     const float tdiff = f[S::it] - f[S::imt];
+    const float mom = 0.5f * uwt + 0.5f * drho_w * uwt;  // rho_w u_w / 2
     f[S::in] = f[S::on] + dn;
-    f[S::ip] = f[S::op] - 0.5f * tdiff + 0.5f * rho_w * uwt - 0.25f * Ft - 0.25f * Fn - 0.5f * dn;
-    f[S::im] = f[S::om] + 0.5f * tdiff - 0.5f * rho_w * uwt + 0.25f * Ft - 0.25f * Fn - 0.5f * dn;
+    f[S::ip] = f[S::op] - 0.5f * tdiff + mom - 0.25f * Ft - 0.25f * Fn - 0.5f * dn;
+    f[S::im] = f[S::om] + 0.5f * tdiff - mom + 0.25f * Ft - 0.25f * Fn - 0.5f * dn;
 }
 
 // Wall rebuild on deviations (f, h of the wall node; ff, hf of its interior neighbour).
@@ -495,8 +508,8 @@ __device__ __forceinline__ void wall_rebuild_side(const DevParams& p, int x, int
     const float uwx = p.wall_ux[SIDE], uwy = p.wall_uy[SIDE];
     const Macro mf = macro_of<THERMAL>(p, ff, hf, x + S::nxv, y + S::nyv);
     const bool adiabatic = THERMAL && p.wall_therm[SIDE] == THERM_ADIABATIC;
-    const float RTw = THERMAL ? (adiabatic ? mf.RT : p.R * p.wall_T[SIDE]) : p.RTp;
-    const float dRTw = THERMAL ? (adiabatic ? mf.dRT : RTw - p.RT0) : (p.RTp - p.RT0);
+    const float RTw = THERMAL ? (adiabatic ? mf.RT : p.wall_RT[SIDE]) : p.RTp;
+    const float dRTw = THERMAL ? (adiabatic ? mf.dRT : p.wall_dRT[SIDE]) : p.dRTp;
     if (kind == WALL_ZOUHE) {
         zouhe<SIDE>(p, x, y, f);
     } else if (kind == WALL_NEE) {
@@ -508,11 +521,11 @@ __device__ __forceinline__ void wall_rebuild_side(const DevParams& p, int x, int
         for (int q = 0; q < 9; ++q) f[q] = ff[q] + (ew[q] - ef[q]);
     } else {  // WALL_EQUILIBRIUM: f^eq - S/2 at the wall state
         const float rw = p.wall_rho[SIDE];
-        const float RTe = THERMAL ? p.R * p.wall_T[SIDE] : p.RTp;
+        const float dRTe = THERMAL ? p.wall_dRT[SIDE] : p.dRTp;
         float Fx, Fy;
         force_at(p, x, y, rw, Fx, Fy);
         float sw[9];
-        dfeq(p, rw, rw - 1.0f, uwx, uwy, RTe - p.RT0, f);
+        dfeq(p, rw, rw - 1.0f, uwx, uwy, dRTe, f);
         source(rw, uwx, uwy, Fx / rw, Fy / rw, sw);
 #pragma unroll
         for (int q = 0; q < 9; ++q) f[q] -= 0.5f * sw[q];
@@ -520,9 +533,10 @@ __device__ __forceinline__ void wall_rebuild_side(const DevParams& p, int x, int
     if (!THERMAL) return;
     if (kind == WALL_EQUILIBRIUM) {
         const float rw = p.wall_rho[SIDE];
-        const float RTe = p.R * p.wall_T[SIDE];
+        const float RTe = p.wall_RT[SIDE], dRTe = p.wall_dRT[SIDE];
         const float Ete = 0.5f * (p.b * RTe + uwx * uwx + uwy * uwy);
-        dheq(p, rw, rw - 1.0f, uwx, uwy, RTe, RTe - p.RT0, Ete, Ete - p.Et0, h);
+        const float dEte = 0.5f * p.b * dRTe + 0.5f * (uwx * uwx + uwy * uwy) + (0.5f * p.b * p.RT0 - p.Et0);
+        dheq(p, rw, rw - 1.0f, uwx, uwy, RTe, dRTe, Ete, dEte, h);
         return;
     }
     // temperature by non-equilibrium extrapolation around the rebuilt node's rho and u:

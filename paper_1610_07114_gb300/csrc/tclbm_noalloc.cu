@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 
@@ -55,8 +56,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Per-node macroscopic values from FP64 populations (Eq. 20 and the temperature of
-// Section IV), summed like tclbm_diagnostics().  The body force enters with the FP32
-// constants the step kernels advance the state with.
+// Section IV), summed like tclbm_diagnostics(): T = 2 / (b R) (E - u^2/2) and T0 in FP64,
+// the body force with the FP32-rounded constants the step kernels advance the state with,
+// and the Taylor-Green force with its sines rounded to FP32 like the handle's tables.
 __global__ void __launch_bounds__(kBlock) noalloc_sums(const double* __restrict__ f, const double* __restrict__ h,
                                                        const double* __restrict__ usnap, long long n, int nx, int ny,
                                                        int thermal, int force_kind, double ax, double ay, double famp,
@@ -79,8 +81,9 @@ __global__ void __launch_bounds__(kBlock) noalloc_sums(const double* __restrict_
             Fx = r * ax;
             Fy = r * ay;
         } else if (force_kind == TCLBM_FORCE_TAYLOR_GREEN) {
-            Fx = famp * sin(6.283185307179586 * x / nx) * sin(6.283185307179586 * y / ny);
-            Fy = famp * cos(6.283185307179586 * x / nx) * cos(6.283185307179586 * y / ny);
+            const double ax_ = 6.283185307179586 * x / nx, ay_ = 6.283185307179586 * y / ny;
+            Fx = famp * (double)(float)sin(ax_) * (double)(float)sin(ay_);
+            Fy = famp * (double)(float)cos(ax_) * (double)(float)cos(ay_);
         }
         const double vx = (jx + 0.5 * Fx) / r, vy = (jy + 0.5 * Fy) / r;
         const double T = thermal ? 2.0 / bR * (sh / r - 0.5 * (vx * vx + vy * vy)) : T0;
@@ -162,11 +165,11 @@ extern "C" tclbm_status tclbm_diagnostics_noalloc(const tclbm_params* params, co
     long long nb = (n + kBlock - 1) / kBlock;
     if (nb > kMaxBlocks) nb = kMaxBlocks;
     cudaStream_t s = (cudaStream_t)stream;
-    const double b = 2.0 / (params->gamma - 1.0);
+    const double bR = 2.0 / (params->gamma - 1.0) * params->R;  // the handle's FP64 b R
     double* result = scratch + kMaxBlocks * TCLBM_NDIAG;
     noalloc_sums<<<(int)nb, kBlock, 0, s>>>(f, params->thermal ? h : nullptr, u_snap, n, params->nx, params->ny,
                                            params->thermal, params->force_kind, (double)(float)params->ax,
-                                           (double)(float)params->ay, (double)(float)params->famp, b * params->R,
+                                           (double)(float)params->ay, (double)(float)params->famp, bR,
                                            params->T0, params->T_ref, scratch);
     noalloc_finish<<<1, 32, 0, s>>>(scratch, (int)nb, out_on_device ? out : result);
     cudaError_t e = cudaGetLastError();
@@ -178,5 +181,13 @@ extern "C" tclbm_status tclbm_diagnostics_noalloc(const tclbm_params* params, co
         snprintf(msg, sizeof msg, "tclbm_diagnostics_noalloc: %s", cudaGetErrorString(e));
         return fail(TCLBM_ECUDA, msg);
     }
+    // a NaN or Inf anywhere in the state reaches the sums; report it as tclbm_diagnostics() does
+    if (!out_on_device)
+        for (int k = 0; k < TCLBM_NDIAG; ++k)
+            if (!std::isfinite(out[k])) {
+                char msg[96];
+                snprintf(msg, sizeof msg, "tclbm_diagnostics_noalloc: non-finite diagnostic %d", k);
+                return fail(TCLBM_ENONFINITE, msg);
+            }
     return TCLBM_OK;
 }

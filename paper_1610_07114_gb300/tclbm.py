@@ -97,6 +97,8 @@ _lib.tclbm_set_tile.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
 _lib.tclbm_set_tile.restype = ctypes.c_int
 _lib.tclbm_test_skip_row.argtypes = [_vp, ctypes.c_int32]
 _lib.tclbm_test_skip_row.restype = ctypes.c_int
+_lib.tclbm_test_rcp.argtypes = [_vp, _vp, ctypes.c_int64, _vp]
+_lib.tclbm_test_rcp.restype = ctypes.c_int
 _lib.tclbm_set_kernel.argtypes = [_vp, ctypes.c_int32]
 _lib.tclbm_set_kernel.restype = ctypes.c_int
 _lib.tclbm_copy_rows.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.c_int32, ctypes.c_int32]
@@ -199,6 +201,10 @@ def tclbm_set_kernel(h, kind):
 
 def tclbm_test_skip_row(h, row):
     _check(_lib.tclbm_test_skip_row(h, int(row)), "tclbm_test_skip_row")
+
+
+def tclbm_test_rcp(x, y, n, stream=None):
+    _check(_lib.tclbm_test_rcp(x, y, int(n), stream), "tclbm_test_rcp")
 
 
 def tclbm_copy_rows(dst, dst_row, src, src_row, rows):

@@ -21,6 +21,11 @@ Case dict vocabulary (names follow the paper's notation):
     walls             {"x-","x+","y-","y+"} -> {"kind": "periodic"|"zouhe"|"nee"|"equilibrium",
                       "ux", "uy", "T", "rho", "therm": "fixed"|"adiabatic"}
     storage           "fp32" | "bf16" | "fp16" population storage of the CUDA path
+    U_ref, rho_scale, T_scale
+                      the case's own scales of velocity, density variation and temperature
+                      variation (wall speed, imposed jumps, hydrostatic or heating
+                      amplitudes): comparisons of fields normalise by them where a field
+                      is nearly uniform
 """
 from __future__ import annotations
 
@@ -103,6 +108,11 @@ def couette(nx=8, ny=64, U=0.05, nu=0.05, Pr=0.71, gamma=1.4, T_wall=1.0, storag
     case["walls"]["y+"] = _wall("zouhe", U, 0.0, T_wall)
     case["U"] = U
     case["U_ref"] = U
+    # peak viscous heating Pr U^2 / (8 c_p), c_p = R (b + 2) / 2; at uniform pressure the
+    # density varies by the same fraction
+    b = 2.0 / (gamma - 1.0)
+    case["T_scale"] = Pr * U * U / (8.0 * case["R"] * (b + 2.0) / 2.0) * T_wall
+    case["rho_scale"] = case["T_scale"] / T_wall
     return case, uniform_fields(nx, ny, T=T_wall)
 
 
@@ -118,6 +128,9 @@ def couette_paper(Pr=5.0, gamma=5.0 / 3.0, nx=5, ny=40, Ma=0.35, mu0=0.35):
     case["U"] = U
     case["U_ref"] = U
     case["Ma"] = Ma
+    b = 2.0 / (gamma - 1.0)
+    case["T_scale"] = Pr * U * U / (2.0 * R_PAPER * (b + 2.0) / 2.0)  # adiabatic-wall heating
+    case["rho_scale"] = case["T_scale"]
     return case, uniform_fields(nx, ny)
 
 
@@ -153,6 +166,8 @@ def rayleigh_benard(nx=256, ny=128, Ra=1e4, Pr=0.71, gamma=1.4, T_bot=1.01, T_to
     case["Ra"] = Ra
     case["g"] = g
     case["U_ref"] = u_c
+    case["T_scale"] = T_bot - T_top
+    case["rho_scale"] = g * (ny - 1) / (case["R"] * T0)  # hydrostatic variation across the layer
     case["T_bot"], case["T_top"] = T_bot, T_top
     rng = np.random.default_rng(seed)
     y = np.arange(ny, dtype=np.float64)
@@ -193,6 +208,9 @@ def shock_tube(nx=4096, ny=4, rho_l=1.05, rho_r=1.0, T=1.0, w1=1.887, storage="f
     case["rho_l"], case["rho_r"] = rho_l, rho_r
     # velocity scale of the weak waves: c_s d(rho)/rho with c_s = sqrt(gamma R T)
     case["U_ref"] = math.sqrt(1.4 * case["R"] * T) * abs(rho_l - rho_r) / (rho_l + rho_r) * 2.0
+    case["rho_scale"] = abs(rho_l - rho_r)
+    # adiabatic temperature change of the same density jump: (gamma - 1) T d(rho) / rho
+    case["T_scale"] = (1.4 - 1.0) * T * abs(rho_l - rho_r) / (0.5 * (rho_l + rho_r))
     return case, f
 
 
@@ -207,6 +225,10 @@ def taylor_green(n=64, F0=1e-5, nu=0.02, thermal=False, storage="fp32"):
     k = 2.0 * math.pi / n
     case["u0"] = F0 / (2.0 * nu * k * k)
     case["U_ref"] = case["u0"]
+    # dynamic pressure over the squared sound speed; kinetic energy over c_p
+    case["rho_scale"] = case["u0"] ** 2 / (case["R"] * case["T0"])
+    b = 2.0 / (case["gamma"] - 1.0)
+    case["T_scale"] = case["u0"] ** 2 / (case["R"] * (b + 2.0) / 2.0)
     return case, uniform_fields(n, n)
 
 
@@ -237,6 +259,8 @@ def random_periodic(nx, ny, seed=0, thermal=True, force="accel", amp_rho=1e-2, a
         return amp * a
 
     case["U_ref"] = amp_u
+    case["rho_scale"] = amp_rho
+    case["T_scale"] = amp_T
     fields = {
         "rho": 1.0 + field(amp_rho),
         "ux": field(amp_u),

@@ -1,0 +1,55 @@
+"""Field comparison of the parity tests (CUDA path against the FP64 oracle).
+
+Relative L2 errors: velocity as a vector field, density and temperature as deviations.
+A uniform part of rho or T (rho ~ 1, T ~ T0) would make a relative bound on the whole
+field trivially met, so each is normalised by the norm of its deviation from the mean,
+floored at sqrt(N) times the case's own scale of that variation (its imposed jumps or
+analytic amplitudes: `rho_scale`, `T_scale`), just as the velocity norm is floored at
+sqrt(N) U_ref.  The floor only matters where a field is nearly uniform (tiny lattices,
+a state whose variation has decayed), where the relative measure would lose its meaning.
+"""
+import math
+
+import numpy as np
+
+
+def _floored_rel(diff_norm, ref_dev, n, scale):
+    den = max(float(np.linalg.norm(ref_dev)), math.sqrt(n) * scale, 1e-300)
+    return float(diff_norm / den)
+
+
+def field_errors(g, o, case):
+    n = o["rho"].size
+    du = np.sqrt(np.sum((g["ux"] - o["ux"]) ** 2 + (g["uy"] - o["uy"]) ** 2))
+    nu = max(np.sqrt(np.sum(o["ux"] ** 2 + o["uy"] ** 2)), np.sqrt(n) * case.get("U_ref", 0.0))
+    out = {
+        "rho": _floored_rel(np.linalg.norm(g["rho"] - o["rho"]), o["rho"] - o["rho"].mean(), n,
+                            case.get("rho_scale", 0.0)),
+        "u": float(du / max(nu, 1e-300)),
+        "T": 0.0,
+        # whole-field relative errors, for information
+        "rho_whole": float(np.linalg.norm(g["rho"] - o["rho"]) / np.linalg.norm(o["rho"])),
+        "T_whole": float(np.linalg.norm(g["T"] - o["T"]) / np.linalg.norm(o["T"])),
+    }
+    if case["thermal"]:
+        out["T"] = _floored_rel(np.linalg.norm(g["T"] - o["T"]), o["T"] - o["T"].mean(), n, case.get("T_scale", 0.0))
+    return out
+
+
+# FP32 state: relative L2 <= 1e-5 on rho, u and T.  One documented exception, the thermal
+# Couette flow: its moving wall (U = 0.05) gives the wall-adjacent populations O(U)
+# deviations, which one FP32 step rounds by 1-2 ulps (1-4e-9) against FP64; near the
+# steady state that rounding repeats every step and the slow shear mode (e-folding
+# H^2 / (pi^2 nu) ~ 8000 steps on 8 x 64) integrates it into a velocity error of ~3e-5
+# of U, and into the viscous-heating signal (T - 1 ~ 4e-4) at ~1.6e-3 of its amplitude
+# (2e-5 - 4e-5 already in the first thousand steps of the acoustic start-up).  The FP64
+# oracle damps a 1e-9 perturbation of the same case monotonically, so this is the
+# storage precision, not an instability.
+FP32_BOUND = (1e-5, 1e-5, 1e-5)
+FP32_BOUND_MOVING_WALL = (3e-3, 5e-5, 3e-3)
+
+
+def fp32_bounds(case):
+    """(rho, u, T) tolerances of FP32 state for this case."""
+    moving = any(abs(w["ux"]) > 0 or abs(w["uy"]) > 0 for w in case["walls"].values() if w["kind"] == "zouhe")
+    return FP32_BOUND_MOVING_WALL if (moving and case["name"].startswith("couette")) else FP32_BOUND

@@ -1,19 +1,20 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerance for FP32 population storage: relative L2 <= 1e-5 on rho, on the velocity
-vector field and on T after the stated step counts, on the same seeded inputs.  The
-velocity norm is floored at sqrt(N) * U_ref (U_ref: the case's velocity scale), since
-FP32 populations of O(0.1) carry an absolute velocity error of ~1e-8 whatever |u| is;
-a near-rest field would otherwise make the ratio meaningless.  One
-step from an identical state must agree population by population to FP32 rounding
-of O(1) arithmetic (abs 2e-6).  Independent tiles must give bit-identical states,
-since every node's arithmetic is the same whatever the launch shape.
+Tolerance for FP32 population storage: relative L2 <= 1e-5 on the velocity vector
+field, and on rho and T as deviations (tests/parity.py: each normalised by its
+deviation from the mean, floored at sqrt(N) times the case's own scale of that
+variation; the velocity norm is floored at sqrt(N) U_ref), after the stated step
+counts, on the same seeded inputs.  One step from an identical state must agree
+population by population to FP32 rounding of O(1) arithmetic (abs 2e-6).  Independent
+tiles must give bit-identical states, since every node's arithmetic is the same
+whatever the launch shape.
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_1610_07114_gb300 import workloads as W
+from tests.parity import field_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -34,23 +35,6 @@ def T():
     return tclbm
 
 
-def rel_l2(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-
-def field_errors(g, o, U_ref=0.0):
-    du = np.sqrt(np.sum((g["ux"] - o["ux"]) ** 2 + (g["uy"] - o["uy"]) ** 2))
-    nu = max(np.sqrt(np.sum(o["ux"] ** 2 + o["uy"] ** 2)), np.sqrt(o["ux"].size) * U_ref)
-    return {
-        "rho": rel_l2(g["rho"], o["rho"]),
-        "u": float(du / max(nu, 1e-300)),
-        "T": rel_l2(g["T"], o["T"]),
-        # deviations from the mean, reported for information
-        "rho_dev": rel_l2(g["rho"] - o["rho"].mean(), o["rho"] - o["rho"].mean()),
-        "T_dev": rel_l2(g["T"] - o["T"].mean(), o["T"] - o["T"].mean()) if np.ptp(o["T"]) > 0 else 0.0,
-    }
-
-
 def run_both(T, case, fields, steps, threads=8):
     lat = T.Lattice(case, fields)
     lat.step(steps)
@@ -63,7 +47,7 @@ def run_both(T, case, fields, steps, threads=8):
 
 def errors(T, case, fields, steps, threads=8):
     g, o = run_both(T, case, fields, steps, threads)
-    return field_errors(g, o, case.get("U_ref", 0.0))
+    return field_errors(g, o, case)
 
 
 def _cases_small():
@@ -123,21 +107,23 @@ def test_fields_after_many_steps(T, name, case, fields):
         assert e[k] <= REL_L2, (name, e)
 
 
-# Near a steady state the per-step change of a population falls below half an FP32 ulp
-# and the stored value stops moving: every node then carries a frozen forcing of about
-# one rounding (~1e-10 here).  The thermal Couette shear flow relaxes over
-# H^2/nu ~ 8e4 steps, which turns that into a 3e-5 velocity error; rho and T stay at
-# ~5e-7.  Its velocity tolerance is therefore 5e-5.
-COUETTE_U_REL_L2 = 5e-5
+# The thermal Couette flow is the one case held to wider FP32 bounds (tests/parity.py:
+# a moving wall's O(U) populations, rounded by 1-2 ulps per step, integrated by the slow
+# shear mode); at 1000 steps, before that integration, u is held to the common 1e-5.
+from tests.parity import fp32_bounds  # noqa: E402
 
 
 def test_thermal_couette_config(T):
     # thermal Couette 8 x 64, U = 0.05, nu = 0.05, Pr = 0.71, gamma = 1.4, 20 000 steps
     case, fields = W.couette(8, 64)
+    b = fp32_bounds(case)
+    assert b[1] == 5e-5
     e = errors(T, case, fields, 20000)
     print("couette", e)
-    assert e["rho"] <= REL_L2 and e["T"] <= REL_L2, e
-    assert e["u"] <= COUETTE_U_REL_L2, e
+    assert e["rho"] <= b[0] and e["u"] <= b[1] and e["T"] <= b[2], e
+    e1 = errors(T, case, fields, 1000)
+    print("couette 1000", e1)
+    assert e1["u"] <= REL_L2, e1
 
 
 def test_rayleigh_benard_config(T):
@@ -400,7 +386,7 @@ def test_tile_kernel_matches_the_oracle_and_is_the_small_lattice_default(T):
     lat.close()
     o = oracle.Oracle(case, fields, threads=8)
     o.step(300)
-    e = field_errors(g, o.moments(), case["U_ref"])
+    e = field_errors(g, o.moments(), case)
     assert e["rho"] <= REL_L2 and e["u"] <= REL_L2 and e["T"] <= REL_L2, e
 
 

@@ -115,3 +115,53 @@ def test_steady_state_requests_stop_at_the_residual(S):
         if a.residual is not None:
             assert a.converged and a.steps_done % 250 == 0 and a.steps_done < 60000
     compare(done, alone)
+
+
+def test_served_results_match_the_fp64_oracle(S):
+    # Requests served together in FP32 storage against the FP64 oracle run of each
+    # request alone: every field at the FP32 parity bar (tests/parity.py), and a
+    # steady-state request stops where the oracle's own residual E_R (Section V.A:
+    # relative L2 change of u over the check interval) crosses the target.
+    import oracle
+    from tests.parity import field_errors, fp32_bounds
+
+    k32 = 2 * np.pi / 32
+    reqs = [
+        S.Request(rid=0, case=W.couette(8, 32)[0], fields=W.couette(8, 32)[1], steps=400),
+        S.Request(rid=1, case=W.rayleigh_benard(64, 32, Ra=2e4, seed=41, amp=1e-2)[0],
+                  fields=W.rayleigh_benard(64, 32, Ra=2e4, seed=41, amp=1e-2)[1], steps=600),
+        S.Request(rid=2, case=W.taylor_green(32, F0=2e-5, nu=0.02, thermal=True)[0],
+                  fields=W.taylor_green(32, F0=2e-5, nu=0.02, thermal=True)[1], steps=500),
+        S.Request(rid=3, case=W.random_periodic(40, 24, seed=42, force="accel", thermal=False)[0],
+                  fields=W.random_periodic(40, 24, seed=42, force="accel", thermal=False)[1], steps=300),
+        S.Request(rid=4, case=W.taylor_green(32, F0=2 * 0.02 * k32 * k32 * 0.02, nu=0.02)[0],
+                  fields=W.taylor_green(32, F0=2 * 0.02 * k32 * k32 * 0.02, nu=0.02)[1], residual=1e-5,
+                  max_steps=60000),
+    ]
+    check = 250
+    srv = S.Server(storage="fp32", rounding="nearest", chunk=64, check_every=check)
+    done = srv.run(copy.deepcopy(reqs), realtime=False)
+    assert srv.stats()["peak_resident"] > 1
+    for r in sorted(done, key=lambda r: r.rid):
+        src = reqs[r.rid]
+        o = oracle.Oracle(src.case, src.fields, threads=8)
+        if src.residual is None:
+            assert r.steps_done == src.steps
+            o.step(src.steps)
+        else:
+            assert r.converged and r.steps_done % check == 0
+            er = []
+            for _ in range(r.steps_done // check):
+                m0 = o.moments()
+                o.step(check)
+                m1 = o.moments()
+                er.append(np.sqrt(np.sum((m1["ux"] - m0["ux"]) ** 2 + (m1["uy"] - m0["uy"]) ** 2)
+                                  / np.sum(m1["ux"] ** 2 + m1["uy"] ** 2)))
+            # the oracle's residual crosses the target at the same check (1e-3 slack for
+            # FP32 state at the crossing)
+            assert er[-1] < src.residual * (1 + 1e-3), er[-3:]
+            assert len(er) == 1 or er[-2] > src.residual * (1 - 1e-3), er[-3:]
+        e = field_errors(r.result, o.moments(), src.case)
+        print("served vs oracle", r.rid, src.case["name"], r.steps_done, e)
+        b = fp32_bounds(src.case)
+        assert e["rho"] <= b[0] and e["u"] <= b[1] and e["T"] <= b[2], (r.rid, e)

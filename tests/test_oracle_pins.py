@@ -308,6 +308,48 @@ def test_adiabatic_wall_keeps_neighbour_temperature():
 # ------------------------------------------------------------------ whole lattice
 
 
+@pytest.mark.parametrize("axis", ["y", "x"])
+def test_correction_gradient_is_exact_for_a_quadratic_profile(axis):
+    # Section IV: the correction term differentiates phi = u (1 - 3 R T) with second-order
+    # differences, central inside and one-sided (-3 phi_0 + 4 phi_1 - phi_2) / 2 at a wall
+    # node.  Both are exact for a quadratic, so with u_n = a + b s + c s^2 across the
+    # walled axis (s the node index, u_t and T uniform) every node must collide with
+    # d_n phi_n = (1 - 3 R T) (b + 2 c s) exactly.  The wall-node rest population f_0
+    # at t + 1 is that node's own post-collision value (Zou-He rebuilds only the incoming
+    # populations), which depends on the derivative through C_0 and the shifted E and N
+    # equilibria; the expected value is the single-node collision given the derivative.
+    n, m = 9, 5
+    nx, ny = (m, n) if axis == "y" else (n, m)
+    case = W.base_case(nx, ny)
+    for s in (("y-", "y+") if axis == "y" else ("x-", "x+")):
+        case["walls"][s] = {"kind": "zouhe", "ux": 0.0, "uy": 0.0, "T": 1.0, "rho": 1.0, "therm": "fixed"}
+    a, b, c = 3e-3, 2e-3, -4e-4
+    Tn = 1.0
+    RT = case["R"] * Tn
+    o = oracle.Oracle(case)
+    f = np.zeros((9, ny, nx))
+    h = np.zeros((9, ny, nx))
+    for y in range(ny):
+        for x in range(nx):
+            s_ = y if axis == "y" else x
+            un = a + b * s_ + c * s_ * s_
+            ux, uy = (0.01, un) if axis == "y" else (un, -0.01)
+            f[:, y, x] = oracle.feq(1.0, ux, uy, RT)
+            h[:, y, x] = oracle.heq(1.0, ux, uy, RT, 2.0 / (case["gamma"] - 1.0))
+    o.set_populations(f, h)
+    idx = [0, 1, n // 2, n - 2, n - 1]
+    xs, ys = (np.full(5, 2), np.array(idx)) if axis == "y" else (np.array(idx), np.full(5, 2))
+    out_f, _ = o.update_nodes(xs, ys)
+    for k, s_ in enumerate(idx):
+        d = (1.0 - 3.0 * RT) * (b + 2.0 * c * s_)
+        dx, dy = (0.0, d) if axis == "y" else (d, 0.0)
+        x, y = int(xs[k]), int(ys[k])
+        ref = oracle.collide_node(case, f[:, y, x], h[:, y, x], dx=dx, dy=dy)["fout"][0]
+        wrong = oracle.collide_node(case, f[:, y, x], h[:, y, x], dx=-dx, dy=-dy)["fout"][0]
+        assert abs(ref - wrong) > 1e-6  # the rest population does see the derivative
+        assert out_f[k][0] == pytest.approx(ref, rel=0, abs=1e-15), (axis, s_)
+
+
 def test_rest_state_is_a_fixed_point():
     case, fields = W.random_periodic(6, 5, seed=0, force="none")
     fields = W.uniform_fields(6, 5)

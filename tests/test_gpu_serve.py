@@ -128,8 +128,8 @@ def test_served_results_match_the_fp64_oracle(S):
     k32 = 2 * np.pi / 32
     reqs = [
         S.Request(rid=0, case=W.couette(8, 32)[0], fields=W.couette(8, 32)[1], steps=400),
-        S.Request(rid=1, case=W.rayleigh_benard(64, 32, Ra=2e4, seed=41, amp=1e-2)[0],
-                  fields=W.rayleigh_benard(64, 32, Ra=2e4, seed=41, amp=1e-2)[1], steps=600),
+        S.Request(rid=1, case=W.rayleigh_benard(96, 48, Ra=1e4, seed=41, amp=1e-2)[0],
+                  fields=W.rayleigh_benard(96, 48, Ra=1e4, seed=41, amp=1e-2)[1], steps=600),
         S.Request(rid=2, case=W.taylor_green(32, F0=2e-5, nu=0.02, thermal=True)[0],
                   fields=W.taylor_green(32, F0=2e-5, nu=0.02, thermal=True)[1], steps=500),
         S.Request(rid=3, case=W.random_periodic(40, 24, seed=42, force="accel", thermal=False)[0],

@@ -17,11 +17,11 @@ from paper_1610_07114_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-# Both paths sum the same FP64 node values (the same FP32 constants in T and the force);
-# only the order of the additions differs, which moves a sum by a few ulps of the sum of
-# the magnitudes of its terms.
+# Both paths sum the same FP64 node values (the same constants in T and the force); only
+# the order of the additions differs, which moves a sum by at most about N ulps of the
+# sum of the magnitudes of its terms (N <= 4608 nodes here).
 REL = 1e-9
-ORDER = 1e-13
+ORDER = 1e-12
 
 
 @pytest.fixture(scope="module")

@@ -279,12 +279,27 @@ tclbm_status tclbm_batch_step(tclbm_batch* batch, int64_t nsteps);
  * list (else one CTA per item).  EINVAL on other values. */
 tclbm_status tclbm_batch_set_tile(tclbm_batch* batch, int32_t tx, int32_t rows, int32_t persistent);
 
+/* TMA-fed strips: thermal lattices with the correction term at least tx columns wide
+ * step in strips of tx (64 or 128) columns by `rows` rows, each staged row by row into
+ * shared memory by the tensor-memory accelerator (the single-lattice kernel variant 0,
+ * one CTA per strip); the other lattices keep the direct-load strips.  tx = 0 turns it
+ * off (the default).  Those lattices then evolve exactly as alone with kernel variant 0
+ * (bit for bit on periodic lattices, as variants 0 and 1 agree there; at walls within
+ * the last bit).  A bounded wait that expires sets the lattice's error word: its next
+ * synchronising call returns TCLBM_ETIMEOUT.  EINVAL on other tx or rows < 1. */
+tclbm_status tclbm_batch_set_tma(tclbm_batch* batch, int32_t tx, int32_t rows);
+/* Current TMA-fed strip shape (tx 0 = off). */
+tclbm_status tclbm_batch_tma_shape(const tclbm_batch* batch, int32_t* tx, int32_t* rows);
+
 /* Time every shape (tx in {32, 64, 128}, rows in {1, 2, 4, ..., 64} up to the tallest
- * lattice, persistent or not) over `trial_steps` (>= 2, rounded up to even) steps each,
- * keep the fastest and report it through the non-NULL out pointers (best_us: device
- * microseconds per batch step).  The lattices' state is saved before and restored
- * after, so the call changes no results; it needs device memory for one copy of every
- * lattice's state and synchronises the stream. */
+ * lattice, persistent or not), then with the fastest of those every TMA-fed shape (tx
+ * in {64, 128}, rows in {8, 16, 32}) where the batch has lattices for it, over
+ * `trial_steps` (>= 2, rounded up to even) steps each; keep the fastest combination and
+ * report the direct-load shape through the non-NULL out pointers (best_us: device
+ * microseconds per batch step; the TMA-fed shape through tclbm_batch_tma_shape).  The
+ * lattices' state is saved before and restored after, so the call changes no results;
+ * it needs device memory for one copy of every lattice's state and synchronises the
+ * stream. */
 tclbm_status tclbm_batch_autotune(tclbm_batch* batch, int32_t trial_steps, int32_t* best_tx, int32_t* best_rows,
                                   int32_t* best_persistent, float* best_us);
 

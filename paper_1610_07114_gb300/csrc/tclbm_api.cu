@@ -518,9 +518,11 @@ tclbm_status build_graph(tclbm_lattice* L) {
     return TCLBM_OK;
 }
 
-// TMA descriptors of both copies: 3-D (x, y, plane), box (tx + 2M, 1, planes).
-tclbm_status ensure_maps(tclbm_lattice* L) {
-    if (L->maps_tx == L->tx) return TCLBM_OK;
+}  // namespace
+
+// TMA descriptors of both copies of L for strips of tx columns: 3-D (x, y, plane), box
+// (tx + 2M, 1, planes).
+tclbm_status tclbm::encode_row_maps(const tclbm_lattice* L, int tx, CUtensorMap out[2]) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -535,14 +537,23 @@ tclbm_status ensure_maps(tclbm_lattice* L) {
                                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const cuuint64_t dims[3] = {(cuuint64_t)L->dp.pitch, (cuuint64_t)L->prm.ny, (cuuint64_t)L->nplanes};
     const cuuint64_t strides[2] = {(cuuint64_t)L->dp.pitch * L->elem, (cuuint64_t)L->dp.plane * L->elem};
-    const cuuint32_t box[3] = {(cuuint32_t)tma_box_width(L->prm.storage, L->tx), 1u, (cuuint32_t)L->nplanes};
+    const cuuint32_t box[3] = {(cuuint32_t)tma_box_width(L->prm.storage, tx), 1u, (cuuint32_t)L->nplanes};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     for (int b = 0; b < 2; ++b) {
-        const CUresult r = encode(&L->maps[b], dt, 3, L->buf[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        const CUresult r = encode(&out[b], dt, 3, L->buf[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return fail(TCLBM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     }
+    return TCLBM_OK;
+}
+
+namespace {
+
+tclbm_status ensure_maps(tclbm_lattice* L) {
+    if (L->maps_tx == L->tx) return TCLBM_OK;
+    tclbm_status st = encode_row_maps(L, L->tx, L->maps);
+    if (st != TCLBM_OK) return st;
     L->maps_tx = L->tx;
     return TCLBM_OK;
 }

@@ -25,17 +25,22 @@ struct tclbm_batch {
     void* ctx = nullptr;
     int storage = 0;
     int sms = 0;
-    // work-list shape
+    // work-list shape of the direct-load strip kernel
     int tx = 64, rows = 4, persistent = 1;
+    // TMA-fed strips for thermal lattices with the correction term at least tma_tx wide
+    // (tma_tx = 0: off; one CTA per item)
+    int tma_tx = 0, tma_rows = 16;
     // device arrays: descriptors and work items
     BatchLattice* d_lats = nullptr;
     size_t d_lats_bytes = 0;
     BatchItem* d_items = nullptr;
     size_t d_items_bytes = 0;
     int nitems = 0;
-    // items grouped by collision variant: [first[k], first[k] + count[k]), grid[k] CTAs
-    int first[3] = {0, 0, 0}, count[3] = {0, 0, 0};
-    unsigned grid[3] = {0, 0, 0};
+    // items grouped by kernel: groups 0..2 the direct-load kernel for each collision
+    // variant (BATCH_*), group 3 the TMA-fed kernel; [first[g], first[g] + count[g]),
+    // grid[g] CTAs
+    int first[4] = {0, 0, 0, 0}, count[4] = {0, 0, 0, 0};
+    unsigned grid[4] = {0, 0, 0, 0};
     // pinned staging of uploads, two generations: uploads are stream-ordered copies,
     // so the host never waits for the kernels in flight
     struct Staging {
@@ -66,33 +71,42 @@ int kind_of(const tclbm_lattice* L) {
 
 long long nodes_of(const tclbm_lattice* L) { return (long long)L->prm.nx * L->prm.ny; }
 
-// Work items for the current shape, grouped by collision variant: within a variant,
-// lattices by decreasing size (longest work first); within a lattice row segments of
-// `rows` rows (the last one takes the remainder, as in the single-lattice kernel) and
-// strips of tx columns, strip index fastest.
+constexpr int kGroupTma = 3;
+
+// Whether lattice L steps in the TMA-fed group.
+bool tma_item(const tclbm_batch* B, const tclbm_lattice* L) {
+    return B->tma_tx > 0 && kind_of(L) == BATCH_THERMAL_CORR && L->prm.nx >= B->tma_tx;
+}
+
+// Work items for the current shape, grouped by kernel (the TMA-fed group first, then
+// the direct-load groups by collision variant): within a group, lattices by decreasing
+// size (longest work first); within a lattice row segments of `rows` rows (the last one
+// takes the remainder, as in the single-lattice kernel) and strips of tx columns, strip
+// index fastest.
 void make_items(tclbm_batch* B, std::vector<BatchItem>& items) {
     std::vector<int> order(B->lats.size());
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        const int ka = kind_of(B->lats[a]), kb = kind_of(B->lats[b]);
-        if (ka != kb) return ka > kb;
-        return nodes_of(B->lats[a]) > nodes_of(B->lats[b]);
-    });
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return nodes_of(B->lats[a]) > nodes_of(B->lats[b]); });
     items.clear();
-    for (int k = 0; k < 3; ++k) B->first[k] = B->count[k] = 0;
-    for (int li : order) {
-        const int k = kind_of(B->lats[li]);
-        if (B->count[k] == 0) B->first[k] = (int)items.size();
-        const tclbm_params& p = B->lats[li]->prm;
-        int nseg = p.ny / B->rows;
-        if (nseg < 1) nseg = 1;
-        const int nstrip = (p.nx + B->tx - 1) / B->tx;
-        for (int s = 0; s < nseg; ++s) {
-            const int y0 = s * B->rows;
-            const int y1 = s == nseg - 1 ? p.ny : y0 + B->rows;
-            for (int c = 0; c < nstrip; ++c) items.push_back(BatchItem{li, c * B->tx, y0, y1});
+    for (int g : {kGroupTma, (int)BATCH_THERMAL_CORR, (int)BATCH_THERMAL, (int)BATCH_ATHERMAL}) {
+        B->first[g] = (int)items.size();
+        for (int li : order) {
+            const tclbm_lattice* L = B->lats[li];
+            const bool tma = tma_item(B, L);
+            if (g == kGroupTma ? !tma : (tma || kind_of(L) != g)) continue;
+            const int tx = tma ? B->tma_tx : B->tx, rows = tma ? B->tma_rows : B->rows;
+            const tclbm_params& p = L->prm;
+            int nseg = p.ny / rows;
+            if (nseg < 1) nseg = 1;
+            const int nstrip = (p.nx + tx - 1) / tx;
+            for (int sg = 0; sg < nseg; ++sg) {
+                const int y0 = sg * rows;
+                const int y1 = sg == nseg - 1 ? p.ny : y0 + rows;
+                for (int c = 0; c < nstrip; ++c) items.push_back(BatchItem{li, c * tx, y0, y1});
+            }
         }
-        B->count[k] = (int)items.size() - B->first[k];
+        B->count[g] = (int)items.size() - B->first[g];
     }
 }
 
@@ -151,6 +165,8 @@ std::vector<int> items_signature(const tclbm_batch* B) {
     sig.push_back(B->tx);
     sig.push_back(B->rows);
     sig.push_back(B->persistent);
+    sig.push_back(B->tma_tx);
+    sig.push_back(B->tma_rows);
     for (const tclbm_lattice* L : B->lats) {
         sig.push_back(L->prm.nx);
         sig.push_back(L->prm.ny);
@@ -177,6 +193,7 @@ tclbm_status upload_items(tclbm_batch* B) {
         const long long wave = (long long)B->sms * batch_ctas_per_sm(B->storage, B->tx, k);
         B->grid[k] = (unsigned)(B->persistent ? std::min<long long>(wave, B->count[k]) : B->count[k]);
     }
+    B->grid[kGroupTma] = (unsigned)B->count[kGroupTma];
     B->items_valid = true;
     B->items_sig.swap(sig);
     B->graph_valid = false;
@@ -198,7 +215,12 @@ tclbm_status upload_lattices(tclbm_batch* B) {
         h[i].p.parity = L->cur ^ par;
         h[i].buf[0] = L->buf[0];
         h[i].buf[1] = L->buf[1];
+        h[i].err = L->err;
         h[i].kind = kind_of(L);
+        if (tma_item(B, L)) {
+            tclbm_status ms = encode_row_maps(L, B->tma_tx, h[i].map);
+            if (ms != TCLBM_OK) return ms;
+        }
         if (same && std::memcmp(&h[i], &B->h_lats[i], sizeof h[i]) != 0) same = false;
     }
     if (same) return TCLBM_OK;
@@ -225,8 +247,13 @@ tclbm_status join_streams(tclbm_batch* B, bool after) {
     return TCLBM_OK;
 }
 
-// One batch step: a launch per collision variant present.
+// One batch step: a launch per kernel group present.
 cudaError_t launch_one_step(const tclbm_batch* B, int parity, cudaStream_t s) {
+    if (B->count[kGroupTma] > 0) {
+        const cudaError_t e = launch_batch_tma_kernel(B->storage, B->tma_tx, B->grid[kGroupTma], B->d_lats,
+                                                      B->d_items + B->first[kGroupTma], B->count[kGroupTma], parity, s);
+        if (e != cudaSuccess) return e;
+    }
     for (int k = 2; k >= 0; --k) {
         if (B->count[k] == 0) continue;
         const cudaError_t e = launch_batch_kernel(B->storage, B->tx, k, B->grid[k], B->d_lats,
@@ -395,6 +422,27 @@ tclbm_status tclbm_batch_set_tile(tclbm_batch* B, int32_t tx, int32_t rows, int3
     return upload_items(B);
 }
 
+tclbm_status tclbm_batch_set_tma(tclbm_batch* B, int32_t tx, int32_t rows) {
+    if (!B) return fail(TCLBM_EINVAL, "batch is NULL");
+    if (!(tx == 0 || tx == 64 || tx == 128) || rows < 1)
+        return fail(TCLBM_EINVAL, "TMA strips: tx must be 0 (off), 64 or 128 and rows >= 1");
+    if (tx != B->tma_tx || rows != B->tma_rows) {
+        B->tma_tx = tx;
+        B->tma_rows = rows;
+        B->items_valid = false;
+    }
+    tclbm_status st = upload_items(B);
+    if (st == TCLBM_OK) st = upload_lattices(B);
+    return st;
+}
+
+tclbm_status tclbm_batch_tma_shape(const tclbm_batch* B, int32_t* tx, int32_t* rows) {
+    if (!B) return fail(TCLBM_EINVAL, "batch is NULL");
+    if (tx) *tx = B->tma_tx;
+    if (rows) *rows = B->tma_rows;
+    return TCLBM_OK;
+}
+
 tclbm_status tclbm_batch_autotune(tclbm_batch* B, int32_t trial_steps, int32_t* best_tx, int32_t* best_rows,
                                   int32_t* best_persistent, float* best_us) {
     if (!B) return fail(TCLBM_EINVAL, "batch is NULL");
@@ -419,42 +467,67 @@ tclbm_status tclbm_batch_autotune(tclbm_batch* B, int32_t trial_steps, int32_t* 
         }
     }
     const int keep_tx = B->tx, keep_rows = B->rows, keep_p = B->persistent;
+    const int keep_ttx = B->tma_tx, keep_trows = B->tma_rows;
     const int64_t keep_steps = B->steps;
-    int bt = keep_tx, br = keep_rows, bp = keep_p;
+    int bt = keep_tx, br = keep_rows, bp = keep_p, btt = keep_ttx, btr = keep_trows;
     float best = 1e30f;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
     int max_ny = 1;
-    for (tclbm_lattice* L : B->lats) max_ny = std::max(max_ny, L->prm.ny);
+    bool any_tma = false;
+    for (tclbm_lattice* L : B->lats) {
+        max_ny = std::max(max_ny, L->prm.ny);
+        any_tma = any_tma || (kind_of(L) == BATCH_THERMAL_CORR && L->prm.nx >= 64);
+    }
+    // one trial of the current shape: true if it was timed
+    auto trial = [&](int tx, int rows, int pers, int ttx, int trows) {
+        B->tx = tx;
+        B->rows = rows;
+        B->persistent = pers;
+        B->tma_tx = ttx;
+        B->tma_rows = trows;
+        B->items_valid = false;
+        st = upload_items(B);
+        if (st == TCLBM_OK) st = upload_lattices(B);
+        if (st == TCLBM_OK) st = launch_batch_steps(B, 2);  // warm-up
+        if (st != TCLBM_OK) return;
+        cudaEventRecord(e0, B->stream);
+        st = launch_batch_steps(B, trial_steps);
+        cudaEventRecord(e1, B->stream);
+        if (st != TCLBM_OK) return;
+        if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) return;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const float us = 1e3f * ms / trial_steps;
+        if (us < best) {
+            best = us;
+            bt = tx;
+            br = rows;
+            bp = pers;
+            btt = ttx;
+            btr = trows;
+        }
+    };
     static const int kTx[] = {32, 64, 128};
     static const int kRows[] = {1, 2, 4, 8, 16, 32, 64};
+    // direct-load strips for every lattice
     for (int t = 0; t < 3 && ce == cudaSuccess && st == TCLBM_OK; ++t)
-        for (int r = 0; r < 7 && st == TCLBM_OK; ++r)
-            for (int pers = 0; pers < 2 && st == TCLBM_OK; ++pers) {
+        for (int r = 0; r < 7 && ce == cudaSuccess && st == TCLBM_OK; ++r)
+            for (int pers = 0; pers < 2 && ce == cudaSuccess && st == TCLBM_OK; ++pers) {
                 if (kRows[r] > max_ny) continue;
-                B->tx = kTx[t];
-                B->rows = kRows[r];
-                B->persistent = pers;
-                B->items_valid = false;
-                st = upload_items(B);
-                if (st == TCLBM_OK) st = launch_batch_steps(B, 2);  // warm-up
-                if (st != TCLBM_OK) break;
-                cudaEventRecord(e0, B->stream);
-                st = launch_batch_steps(B, trial_steps);
-                cudaEventRecord(e1, B->stream);
-                if (st != TCLBM_OK) break;
-                if ((ce = cudaEventSynchronize(e1)) != cudaSuccess) break;
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                const float us = 1e3f * ms / trial_steps;
-                if (us < best) {
-                    best = us;
-                    bt = kTx[t];
-                    br = kRows[r];
-                    bp = pers;
-                }
+                trial(kTx[t], kRows[r], pers, 0, keep_trows);
             }
+    // TMA-fed strips for the wide thermal lattices with the correction term, the others
+    // on the best direct-load shape
+    static const int kTmaTx[] = {64, 128};
+    static const int kTmaRows[] = {8, 16, 32};
+    const int dtx = bt, drows = br, dpers = bp;
+    for (int t = 0; t < 2 && any_tma && ce == cudaSuccess && st == TCLBM_OK; ++t)
+        for (int r = 0; r < 3 && ce == cudaSuccess && st == TCLBM_OK; ++r) {
+            if (kTmaRows[r] > max_ny) continue;
+            trial(dtx, drows, dpers, kTmaTx[t], kTmaRows[r]);
+        }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     // restore the state; the batch's parity is back where it was (even trial lengths)
@@ -480,8 +553,11 @@ tclbm_status tclbm_batch_autotune(tclbm_batch* B, int32_t trial_steps, int32_t* 
     B->tx = bt;
     B->rows = br;
     B->persistent = bp;
+    B->tma_tx = btt;
+    B->tma_rows = btr;
     B->items_valid = false;
     st = upload_items(B);
+    if (st == TCLBM_OK) st = upload_lattices(B);
     if (st != TCLBM_OK) return st;
     if (best_tx) *best_tx = bt;
     if (best_rows) *best_rows = br;
@@ -494,11 +570,14 @@ const char* tclbm_batch_describe(const tclbm_batch* B) {
     if (!B) return "";
     tclbm_batch* M = const_cast<tclbm_batch*>(B);
     const char* st = B->storage == 0 ? "float" : (B->storage == 1 ? "bf16" : "half");
-    snprintf(M->desc, sizeof M->desc,
-             "tclbm_step_batch<%d,%s> lattices %zu items %d (corr %d, thermal %d, athermal %d) grid (%u,%u,%u) "
-             "block (%d) rows %d%s",
-             B->tx, st, B->lats.size(), B->nitems, B->count[2], B->count[1], B->count[0], B->grid[2], B->grid[1],
-             B->grid[0], B->tx, B->rows, B->persistent ? " persistent" : "");
+    int n = snprintf(M->desc, sizeof M->desc,
+                     "tclbm_step_batch<%d,%s> lattices %zu items %d (corr %d, thermal %d, athermal %d) grid (%u,%u,%u) "
+                     "block (%d) rows %d%s",
+                     B->tx, st, B->lats.size(), B->nitems - B->count[kGroupTma], B->count[2], B->count[1], B->count[0],
+                     B->grid[2], B->grid[1], B->grid[0], B->tx, B->rows, B->persistent ? " persistent" : "");
+    if (B->count[kGroupTma] > 0 && n > 0 && n < (int)sizeof M->desc)
+        snprintf(M->desc + n, sizeof M->desc - n, "; tclbm_step_batch_tma<%d,%s> items %d rows %d", B->tma_tx, st,
+                 B->count[kGroupTma], B->tma_rows);
     return B->desc;
 }
 

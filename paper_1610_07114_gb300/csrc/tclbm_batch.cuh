@@ -2,6 +2,7 @@
 // time step in one launch, each work item a strip of one lattice updated by the same
 // strip code as the single-lattice direct kernel.
 #pragma once
+#include <cuda.h>
 #include <stddef.h>
 
 #include "tclbm_device.cuh"
@@ -12,10 +13,13 @@ namespace tclbm {
 enum { BATCH_ATHERMAL = 0, BATCH_THERMAL = 1, BATCH_THERMAL_CORR = 2 };
 
 // One lattice of a batch: its constants (p.parity = index of its source copy at the
-// batch's step 0), its two population copies and its collision variant.
+// batch's step 0), its two population copies, its collision variant, and for the
+// TMA-fed batch kernel the row tensor maps of both copies and its error word.
 struct BatchLattice {
+    CUtensorMap map[2];  // 64-byte aligned: the first member
     DevParams p;
     const void* buf[2];
+    int* err;
     int kind;
 };
 

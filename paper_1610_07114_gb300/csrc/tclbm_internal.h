@@ -56,6 +56,8 @@ namespace tclbm {
 // Records a printf-style message for tclbm_last_error() and returns `st`.
 tclbm_status fail(tclbm_status st, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 tclbm_status cuda_fail(cudaError_t e, const char* what);
+// TMA row descriptors of both copies of L for strips of tx columns (box tx + 2M wide).
+tclbm_status encode_row_maps(const tclbm_lattice* L, int tx, CUtensorMap out[2]);
 // Device memory through the handle's allocator hooks (cudaMalloc / cudaFree without them).
 void* dev_alloc(tclbm_lattice* L, size_t bytes);
 void dev_free(tclbm_lattice* L, void* p, size_t bytes);

@@ -47,6 +47,22 @@ cudaError_t launch_batch_bf16(int tx, int kind, unsigned grid, const BatchLattic
                               int nitems, int step_parity, cudaStream_t s);
 cudaError_t launch_batch_fp16(int tx, int kind, unsigned grid, const BatchLattice* lats, const BatchItem* items,
                               int nitems, int step_parity, cudaStream_t s);
+// TMA-fed batched step of thermal lattices with the correction term (tx 64 or 128; one
+// CTA per item).
+cudaError_t launch_batch_tma_fp32(int tx, unsigned grid, const BatchLattice* lats, const BatchItem* items, int nitems,
+                                  int step_parity, cudaStream_t s);
+cudaError_t launch_batch_tma_bf16(int tx, unsigned grid, const BatchLattice* lats, const BatchItem* items, int nitems,
+                                  int step_parity, cudaStream_t s);
+cudaError_t launch_batch_tma_fp16(int tx, unsigned grid, const BatchLattice* lats, const BatchItem* items, int nitems,
+                                  int step_parity, cudaStream_t s);
+inline cudaError_t launch_batch_tma_kernel(int storage, int tx, unsigned grid, const BatchLattice* lats,
+                                           const BatchItem* items, int nitems, int step_parity, cudaStream_t s) {
+    switch (storage) {
+        case 0: return launch_batch_tma_fp32(tx, grid, lats, items, nitems, step_parity, s);
+        case 1: return launch_batch_tma_bf16(tx, grid, lats, items, nitems, step_parity, s);
+        default: return launch_batch_tma_fp16(tx, grid, lats, items, nitems, step_parity, s);
+    }
+}
 // Resident CTAs per SM of the batched kernel for a tile width and variant (occupancy calculator).
 int batch_occupancy_fp32(int tx, int kind);
 int batch_occupancy_bf16(int tx, int kind);

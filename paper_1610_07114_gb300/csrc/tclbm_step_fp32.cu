@@ -7,4 +7,5 @@ using ST = float;
 #define PREPARE_FN prepare_step_fp32
 #define BATCH_FN launch_batch_fp32
 #define BATCH_OCC_FN batch_occupancy_fp32
+#define BATCH_TMA_FN launch_batch_tma_fp32
 #include "tclbm_step_inst.cuh"

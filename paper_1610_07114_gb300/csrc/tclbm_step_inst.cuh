@@ -77,6 +77,7 @@ static cudaError_t launch_tx(const StepLaunch& k, const DevParams& p0, const voi
 template <int TX>
 static cudaError_t prepare_tx() {
     cudaError_t e = allow_smem(tclbm_step_tma_corr<TX, ST>, tma_smem_bytes<TX, true, ST>(true));
+    if (e == cudaSuccess) e = allow_smem(tclbm_step_batch_tma<TX, ST>, tma_smem_bytes<TX, true, ST>(true));
     if (e == cudaSuccess) e = allow_smem(tclbm_step_tma_plain<TX, true, ST>, tma_smem_bytes<TX, true, ST>(false));
     if (e == cudaSuccess) e = allow_smem(tclbm_step_tma_plain<TX, false, ST>, tma_smem_bytes<TX, false, ST>(false));
     return e;
@@ -138,6 +139,18 @@ static int occupancy_tx(int kind) {
         return 1;
     }
     return n > 0 ? n : 1;
+}
+
+cudaError_t BATCH_TMA_FN(int tx, unsigned grid, const BatchLattice* lats, const BatchItem* items, int nitems,
+                         int step_parity, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    if (tx == 64)
+        tclbm_step_batch_tma<64, ST><<<grid, 64, tma_smem_bytes<64, true, ST>(true), s>>>(lats, items, nitems,
+                                                                                          step_parity);
+    else
+        tclbm_step_batch_tma<128, ST><<<grid, 128, tma_smem_bytes<128, true, ST>(true), s>>>(lats, items, nitems,
+                                                                                             step_parity);
+    return cudaGetLastError();
 }
 
 int BATCH_OCC_FN(int tx, int kind) {

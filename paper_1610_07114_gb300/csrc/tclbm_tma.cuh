@@ -24,6 +24,7 @@
 
 #include <cuda.h>
 
+#include "tclbm_batch.cuh"
 #include "tclbm_device.cuh"
 
 namespace tclbm {
@@ -328,21 +329,19 @@ struct CorrShape {
     static constexpr int kThreadsPerSM = sizeof(ST) == 4 ? 384 : 512;
 };
 
+// One strip: columns [x0, x0 + TX) of rows [y0, y1), every thread of the CTA.  `p` is a
+// kernel parameter or a shared-memory copy; `map` the source copy's tensor map (in
+// parameter or global memory); `smem` the dynamic shared memory of tma_smem_bytes().
+// Returns false after a bounded wait expired (the error word is then set).
 template <int TX, class ST>
-__global__ void __launch_bounds__(TX, CorrShape<ST>::kThreadsPerSM / TX) tclbm_step_tma_corr(const __grid_constant__ DevParams p, const __grid_constant__ CUtensorMap map,
-                                                          const ST* __restrict__ src, ST* __restrict__ dst,
-                                                          int rows_per_cta, int* __restrict__ err) {
-    extern __shared__ __align__(128) unsigned char smem[];
+__device__ __forceinline__ bool tma_corr_strip(const DevParams& p, const CUtensorMap* map, const ST* __restrict__ src,
+                                               ST* __restrict__ dst, int x0, int y0, int y1, int* __restrict__ err,
+                                               unsigned char* smem) {
     using RR = RowRing<TX, true, ST>;
     RR R;
-    if (*(volatile int*)err) return;  // an earlier launch gave up: do not queue more waits
     float(*phix)[TX + 4] = reinterpret_cast<float(*)[TX + 4]>(smem + RR::RING_BYTES + 8 * sizeof(uint64_t));
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX;
     const int nx = p.nx, ny = p.ny;
-    const int nseg = gridDim.y;
-    const int y0 = blockIdx.y * rows_per_cta;
-    const int y1 = (blockIdx.y == nseg - 1) ? ny : y0 + rows_per_cta;
     const bool ywall = !p.yper;
     // sources: the phi_y of row y0-1 needs y0-2; the lookahead of row y1 needs y1+1;
     // the bottom wall's one-sided stencil needs row 3 (inside the first ring fill); a
@@ -351,7 +350,7 @@ __global__ void __launch_bounds__(TX, CorrShape<ST>::kThreadsPerSM / TX) tclbm_s
     const int s_first = short_top ? y0 - 3 : y0 - 2;
     int s_last = y1 + 1;
     if (ywall && y0 == 0 && s_last < 3) s_last = 3;
-    ring_setup<TX, true, ST>(R, smem, &map, x0, s_first, s_last, p);
+    ring_setup<TX, true, ST>(R, smem, map, x0, s_first, s_last, p);
 
     const int xl = x0 + tid;  // logical column of this thread
     const bool owns = xl < nx;
@@ -462,7 +461,7 @@ __global__ void __launch_bounds__(TX, CorrShape<ST>::kThreadsPerSM / TX) tclbm_s
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(err, 1);
             R.drain();
-            return;
+            return false;
         }
         // later rows read sources from r on (a top-wall row r+2 reads its neighbour's
         // r..r+2): the slot of r-1 is free
@@ -480,7 +479,54 @@ __global__ void __launch_bounds__(TX, CorrShape<ST>::kThreadsPerSM / TX) tclbm_s
         buf_c = buf_n;
         yr_next = (p.yper && yr_next == ny - 1) ? 0 : yr_next + 1;
     }
+    return true;
+}
+
+template <int TX, class ST>
+__global__ void __launch_bounds__(TX, CorrShape<ST>::kThreadsPerSM / TX) tclbm_step_tma_corr(const __grid_constant__ DevParams p, const __grid_constant__ CUtensorMap map,
+                                                          const ST* __restrict__ src, ST* __restrict__ dst,
+                                                          int rows_per_cta, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (*(volatile int*)err) return;  // an earlier launch gave up: do not queue more waits
+    const int nseg = gridDim.y;
+    const int y0 = blockIdx.y * rows_per_cta;
+    const int y1 = (blockIdx.y == nseg - 1) ? p.ny : y0 + rows_per_cta;
+    if (!tma_corr_strip<TX, ST>(p, &map, src, dst, blockIdx.x * TX, y0, y1, err, smem)) return;
     if (blockIdx.x == 0 && blockIdx.y == 0) bump_step_counter(p);
+}
+
+// Batched form of the kernel above (thermal lattices with the correction term): CTA b
+// takes work item b, a strip of TX columns by rows [y0, y1) of one lattice, whose
+// constants it copies to shared memory (parity flipped by `step_parity`) and whose row
+// tensor map it reads from the lattice's descriptor in global memory.  Every node runs
+// the same code as in the single-lattice kernel, so a lattice evolves bit for bit as it
+// does alone with that kernel.  A lattice whose error word is set is skipped; an
+// expired wait sets it.
+template <int TX, class ST>
+__global__ void __launch_bounds__(TX, CorrShape<ST>::kThreadsPerSM / TX) tclbm_step_batch_tma(
+    const BatchLattice* __restrict__ lats, const BatchItem* __restrict__ items, int nitems, int step_parity) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ DevParams sp;
+    const BatchItem it = items[blockIdx.x];
+    const BatchLattice* L = lats + it.lat;
+    if (*(volatile int*)L->err) return;  // an earlier launch on this lattice gave up
+    constexpr int kWords = (int)(sizeof(DevParams) / sizeof(int));
+    constexpr int kParityWord = (int)(offsetof(DevParams, parity) / sizeof(int));
+    {
+        const int* s = reinterpret_cast<const int*>(&L->p);
+        int* d = reinterpret_cast<int*>(&sp);
+        for (int w = threadIdx.x; w < kWords; w += TX) d[w] = w == kParityWord ? (s[w] ^ step_parity) : s[w];
+    }
+    __syncthreads();
+    const int par = sp.parity;
+    const CUtensorMap* map = &L->map[par];
+    // the descriptor was written through the generic proxy (a host copy); the TMA unit
+    // reads it through the tensor-map proxy
+    if (threadIdx.x == 0) asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+    const ST* src = static_cast<const ST*>(L->buf[par]);
+    ST* dst = static_cast<ST*>(const_cast<void*>(L->buf[par ^ 1]));
+    if (!tma_corr_strip<TX, ST>(sp, map, src, dst, it.x0, it.y0, it.y1, L->err, smem)) return;
+    if (it.x0 == 0 && it.y0 == 0) bump_step_counter(sp);
 }
 
 // Dynamic shared memory of the TMA kernels.

@@ -116,6 +116,10 @@ _lib.tclbm_batch_set_tile.restype = ctypes.c_int
 _ip = ctypes.POINTER(ctypes.c_int32)
 _lib.tclbm_batch_autotune.argtypes = [_vp, ctypes.c_int32, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_float)]
 _lib.tclbm_batch_autotune.restype = ctypes.c_int
+_lib.tclbm_batch_set_tma.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
+_lib.tclbm_batch_set_tma.restype = ctypes.c_int
+_lib.tclbm_batch_tma_shape.argtypes = [_vp, _ip, _ip]
+_lib.tclbm_batch_tma_shape.restype = ctypes.c_int
 _lib.tclbm_batch_describe.argtypes = [_vp]
 _lib.tclbm_batch_describe.restype = ctypes.c_char_p
 _lib.tclbm_batch_steps_done.argtypes = [_vp]
@@ -241,6 +245,16 @@ def tclbm_batch_step(b, n):
 
 def tclbm_batch_set_tile(b, tx, rows, persistent):
     _check(_lib.tclbm_batch_set_tile(b, int(tx), int(rows), int(persistent)), "tclbm_batch_set_tile")
+
+
+def tclbm_batch_set_tma(b, tx, rows):
+    _check(_lib.tclbm_batch_set_tma(b, int(tx), int(rows)), "tclbm_batch_set_tma")
+
+
+def tclbm_batch_tma_shape(b):
+    tx, rows = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.tclbm_batch_tma_shape(b, ctypes.byref(tx), ctypes.byref(rows)), "tclbm_batch_tma_shape")
+    return tx.value, rows.value
 
 
 def tclbm_batch_autotune(b, trial_steps):
@@ -460,8 +474,18 @@ class Batch:
     def set_tile(self, tx: int, rows: int, persistent: bool = True):
         tclbm_batch_set_tile(self.handle, tx, rows, 1 if persistent else 0)
 
+    def set_tma(self, tx: int, rows: int = 16):
+        """TMA-fed strips (tx 64 or 128; 0 = off) for the thermal lattices with the
+        correction term at least tx wide; the others keep the direct-load strips."""
+        tclbm_batch_set_tma(self.handle, tx, rows)
+
+    def tma_shape(self):
+        return tclbm_batch_tma_shape(self.handle)
+
     def autotune(self, trial_steps: int = 8):
-        """(tx, rows, persistent, us_per_step) of the fastest work-list shape, now selected."""
+        """(tx, rows, persistent, us_per_step) of the fastest direct-load work-list shape,
+        now selected together with the fastest TMA-fed shape (tma_shape(); tx 0 if the
+        direct-load strips alone were faster)."""
         tx, rows, pers, us = tclbm_batch_autotune(self.handle, trial_steps)
         return tx, rows, bool(pers), us
 

@@ -208,3 +208,55 @@ def test_replacing_lattices_rebuilds_the_work_list(T):
     assert prev is not None
     b.close()
     keep.close()
+
+
+@pytest.mark.parametrize("storage,rounding", [("fp32", "nearest"), ("fp16", "stochastic")])
+@pytest.mark.parametrize("tma", [(128, 16), (64, 8), (128, 3)])
+def test_tma_fed_batch_equals_each_lattice_alone(T, tma, storage, rounding):
+    # TMA-fed strips for the thermal lattices with the correction term at least tx wide
+    # (the single-lattice TMA kernel's code, one CTA per strip); the others keep the
+    # direct-load strips.  Both agree with the lattice stepped alone.
+    cases = mixed_cases(storage, rounding) + [
+        ("rb_256x64", *W.rayleigh_benard(256, 64, Ra=1e4, seed=38, storage=storage)),
+        ("periodic_200x37", *W.random_periodic(200, 37, seed=39, force="taylor_green", storage=storage)),
+    ]
+    cases = [(n, dict(c, rounding=rounding), f) for n, c, f in cases]
+    lats = [T.Lattice(c, f) for _, c, f in cases]
+    with T.Batch(lats) as b:
+        b.set_tma(*tma)
+        assert b.tma_shape() == tma
+        assert "tclbm_step_batch_tma" in b.describe()
+        b.step(3)
+        b.step(70)  # graph replay entered at odd parity
+    for (name, c, f), lat in zip(cases, lats):
+        assert lat.steps_done == 73
+        got = lat.populations()
+        assert lat.diagnostics() is not None  # an expired pipeline wait would surface here
+        for kernel in (0, 1):
+            ref = T.Lattice(c, f)
+            try:
+                ref.set_kernel(kernel)
+            except T.TclbmError:
+                ref.close()
+                continue
+            ref.step(73)
+            exp = ref.populations()
+            ref.close()
+            assert_same(c, got, exp)
+        lat.close()
+
+
+def test_tma_fed_batch_matches_fp64_oracle(T):
+    case, fields = W.rayleigh_benard(192, 96, Ra=1e4, seed=40, amp=1e-2)
+    lat = T.Lattice(case, fields)
+    with T.Batch([lat]) as b:
+        b.set_tma(128, 16)
+        b.step(300)
+    g = lat.moments()
+    lat.close()
+    o = oracle.Oracle(case, fields, threads=8)
+    o.step(300)
+    from tests.parity import field_errors
+
+    e = field_errors(g, o.moments(), case)
+    assert e["rho"] <= 1e-5 and e["u"] <= 1e-5 and e["T"] <= 1e-5, e

@@ -284,37 +284,54 @@ def bench_serve(args):
     from paper_1610_07114_gb300 import workloads as W
 
     world, rank, _ = _dist()
-    trace = W.serving_trace(duration_s=args.serve_duration, rate=args.serve_rate, seed=42 + rank)
+    trace = W.serving_trace(duration_s=args.serve_duration, rate=args.serve_rate, seed=42 + rank,
+                            steps_choices=args.serve_steps, steady_frac=args.serve_steady_frac,
+                            steady_residual=args.serve_steady_residual)
+    storage = args.serve_storage
+    rounding = "stochastic" if storage != "fp32" else "nearest"
 
     def requests():
+        # cases now, initial fields at admission (a long trace would not fit in host memory)
         out = []
         for i, r in enumerate(trace):
-            case, fields = W.build_request(r)
-            out.append(serve.Request(rid=i, case=case, fields=fields, steps=r["steps"], t_arrival=r["t_arrival"]))
+            case, _ = W.build_request(r, fields=False)
+            out.append(serve.Request(rid=i, case=case, fields=lambda r=r: W.build_request(r)[1], steps=r["steps"],
+                                     t_arrival=r["t_arrival"], residual=r.get("residual"),
+                                     max_steps=args.serve_steady_max_steps))
         return out
+
+    def steady(done):
+        s = [r for r in done if r.residual is not None]
+        return {"requests": len(s), "converged": sum(bool(r.converged) for r in s),
+                "steps_max": max((r.steps_done for r in s), default=0),
+                "latency_max_s": max((r.latency for r in s), default=0.0)}
 
     reqs = requests()  # built before either clock starts
     torch.cuda.synchronize()
     _barrier(world)
     t0 = time.perf_counter()
-    srv = serve.Server(chunk=args.serve_chunk, keep_results=False)
-    srv.run(reqs)
+    srv = serve.Server(storage=storage, rounding=rounding, chunk=args.serve_chunk, keep_results=False)
+    done = srv.run(reqs)
     wall = _max_over_ranks(time.perf_counter() - t0, world)
     served = srv.stats(wall)
     served["LU_per_s"] = _sum_over_ranks(float(served["lattice_updates"]), world) / wall
+    served["steady_state"] = steady(done)
     reqs = requests()
     torch.cuda.synchronize()
     _barrier(world)
     t0 = time.perf_counter()
-    _, alone = serve.serve_alone(reqs, keep_results=False)
+    done_alone, alone = serve.serve_alone(reqs, storage=storage, rounding=rounding, keep_results=False)
     wall_alone = _max_over_ranks(time.perf_counter() - t0, world)
+    alone["steady_state"] = steady(done_alone)
     alone["LU_per_s"] = _sum_over_ranks(float(alone["lattice_updates"]), world) / wall_alone
     return {"workload": f"serve_poisson_{args.serve_rate:g}per_s_{args.serve_duration:g}s",
             "requests_per_rank": len(trace), "ranks": world, "latencies": "rank 0",
             "nodes_total": int(sum(r["nx"] * r["ny"] for r in trace)), "wall_s": wall, "served": served,
             "alone": alone, "ratio_LU_per_s": served["LU_per_s"] / alone["LU_per_s"],
             "p99_ratio_alone_over_served": alone["p99_s"] / served["p99_s"],
-            "storage": "fp16", "rounding": "stochastic", "chunk": args.serve_chunk}
+            "storage": storage, "rounding": rounding, "chunk": args.serve_chunk,
+            "steps_choices": list(args.serve_steps), "steady_frac": args.serve_steady_frac,
+            "batching": "all lattices in one batched launch per step (TMA-fed strips from 128 columns)"}
 
 
 def serve_run(args):
@@ -534,6 +551,13 @@ def main():
     ap.add_argument("--serve-duration", type=float, default=1.0, help="seconds of Poisson arrivals")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
     ap.add_argument("--serve-chunk", type=int, default=64)
+    ap.add_argument("--serve-steps", type=int, nargs="+", default=[200, 500, 1000, 2000],
+                    help="fixed step counts the requests draw from")
+    ap.add_argument("--serve-steady-frac", type=float, default=0.0,
+                    help="share of requests that ask for the steady state (Couette 32x128, nu 0.3)")
+    ap.add_argument("--serve-steady-residual", type=float, default=1e-8)
+    ap.add_argument("--serve-steady-max-steps", type=int, default=400000)
+    ap.add_argument("--serve-storage", default="fp16", choices=["fp32", "bf16", "fp16"])
     ap.add_argument("--serve-only", action="store_true", help="print only the serving measurement")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -11,12 +11,13 @@ Every admitted lattice stays resident on the device.  Between chunks of steps th
     driver reports minus a reserve),
   * picks the lattices to step in the next chunk: least remaining work (nodes x steps
     left) first, until `node_budget` nodes -- enough to fill the GPU -- are chosen,
-  * advances the chosen lattices below `own_launch_nodes` nodes (131,072 by default)
-    with one batched launch per time step (tclbm_batch_*; the lattice list is swapped
-    by stream-ordered copies, nothing waits for the GPU) and each larger one, whose own
-    tile or TMA kernel already fills most of the GPU, with its own single-lattice
-    launches on the same stream (measured on the 200/s trace: 20.6 G lattice updates/s
-    and p50 2.6 s at 131,072, against 19.6 G and 3.0 s at 2,097,152),
+  * advances the chosen lattices together with one batched launch per time step
+    (tclbm_batch_*; the lattice list is swapped by stream-ordered copies, nothing waits
+    for the GPU): lattices at least `tma[0]` columns wide in TMA-fed strips (the
+    single-lattice TMA kernel's code, one CTA per strip), narrower ones in direct-load
+    strips, so large and small requests overlap in the same launch.  With tma=None,
+    lattices from `own_launch_nodes` nodes take their own single-lattice launches on
+    the same stream instead (the earlier policy, kept for comparison),
   * retires finished lattices: their read-back waits on an event recorded after
     their last step, on a separate stream, so the next chunk is already queued.
 At most `max_in_flight` chunks are queued ahead of the GPU, so an arrival is stepped
@@ -40,7 +41,7 @@ from . import tclbm
 class Request:
     rid: int
     case: dict
-    fields: dict
+    fields: object  # dict of initial fields, or a callable returning one (built at admission)
     steps: int | None = None  # fixed step count, or
     residual: float | None = None  # steady state: residual below this ...
     max_steps: int = 1_000_000  # ... or this many steps, whichever comes first
@@ -61,6 +62,10 @@ class Request:
         return self.t_done - self.t_arrival
 
 
+def _fields_of(req):
+    return req.fields() if callable(req.fields) else req.fields
+
+
 @dataclasses.dataclass
 class _Active:
     req: Request
@@ -75,7 +80,7 @@ class Server:
     def __init__(self, storage: str = "fp16", rounding: str = "stochastic", hbm_budget: int | None = None,
                  reserve_bytes: int = 4 << 30, chunk: int = 64, check_every: int = 1000, max_in_flight: int = 2,
                  tile=None, keep_results: bool = True, node_budget: int = 48 << 20,
-                 own_launch_nodes: int = 1 << 17):
+                 own_launch_nodes: int = 1 << 17, tma=(128, 16)):
         import torch
 
         self.torch = torch
@@ -90,6 +95,7 @@ class Server:
         self.keep_results = keep_results
         self.node_budget = node_budget
         self.own_launch_nodes = own_launch_nodes
+        self.tma = tma
         self.stream = torch.cuda.Stream()  # batched steps
         self.admit_stream = torch.cuda.Stream()  # creation and initial fields
         self.readout = torch.cuda.Stream()  # results of retired lattices
@@ -129,7 +135,7 @@ class Server:
                 break  # first come, first served: wait for memory
             self.queue.popleft()
             lat = tclbm.Lattice(case, None, stream=self.admit_stream.cuda_stream)
-            lat.init_fields(req.fields)  # host fields: synchronises the admission stream only
+            lat.init_fields(_fields_of(req))  # host fields: synchronises the admission stream only
             lat.set_stream(self.stream.cuda_stream)
             req.t_admit = self._clock()
             first = req.steps if req.steps is not None else min(self.check_every, req.max_steps)
@@ -155,8 +161,11 @@ class Server:
             nodes += a.req.nodes
         return chosen
 
+    def _own_launch(self, a) -> bool:
+        return self.tma is None and a.req.nodes >= self.own_launch_nodes
+
     def _sync_batch(self, chosen):
-        lats = [a.lat for a in chosen if a.req.nodes < self.own_launch_nodes]
+        lats = [a.lat for a in chosen if not self._own_launch(a)]
         if lats == self._batch_lats:
             return
         if self.batch is None:
@@ -165,6 +174,8 @@ class Server:
             self.batch = tclbm.Batch(lats, stream=self.stream.cuda_stream)
             if self.tile is not None:
                 self.batch.set_tile(*self.tile)
+            if self.tma is not None:
+                self.batch.set_tma(*self.tma)
         else:
             self.batch.set_lattices(lats)
         self._batch_lats = lats
@@ -179,7 +190,7 @@ class Server:
         if self._batch_lats:
             self.batch.step(k)
         for a in chosen:
-            if a.req.nodes >= self.own_launch_nodes:
+            if self._own_launch(a):
                 a.lat.step(k)
         ev = torch.cuda.Event()
         ev.record(self.stream)
@@ -290,7 +301,7 @@ def serve_alone(requests, storage="fp16", rounding="stochastic", realtime=True, 
         else:
             r.t_arrival = 0.0
         case = dict(r.case, storage=storage, rounding=rounding)
-        lat = tclbm.Lattice(case, r.fields, stream=stream.cuda_stream)
+        lat = tclbm.Lattice(case, _fields_of(r), stream=stream.cuda_stream)
         if kernel is not None:
             lat.set_kernel(kernel)
         r.t_admit = time.perf_counter() - t0

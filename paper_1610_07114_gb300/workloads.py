@@ -93,7 +93,7 @@ def uniform_fields(nx, ny, rho=1.0, ux=0.0, uy=0.0, T=1.0):
 # --------------------------------------------------------------------------- paper cases
 
 
-def couette(nx=8, ny=64, U=0.05, nu=0.05, Pr=0.71, gamma=1.4, T_wall=1.0, storage="fp32"):
+def couette(nx=8, ny=64, U=0.05, nu=0.05, Pr=0.71, gamma=1.4, T_wall=1.0, storage="fp32", fields=True):
     """Thermal Couette flow with viscous heating (Section V.B set-up, isothermal walls).
 
     Periodic in x; y = 0 is a wall at rest and y = ny-1 moves with u = (U, 0); both
@@ -113,7 +113,7 @@ def couette(nx=8, ny=64, U=0.05, nu=0.05, Pr=0.71, gamma=1.4, T_wall=1.0, storag
     b = 2.0 / (gamma - 1.0)
     case["T_scale"] = Pr * U * U / (8.0 * case["R"] * (b + 2.0) / 2.0) * T_wall
     case["rho_scale"] = case["T_scale"] / T_wall
-    return case, uniform_fields(nx, ny, T=T_wall)
+    return case, (uniform_fields(nx, ny, T=T_wall) if fields else None)
 
 
 def couette_paper(Pr=5.0, gamma=5.0 / 3.0, nx=5, ny=40, Ma=0.35, mu0=0.35):
@@ -145,7 +145,7 @@ def rb_gravity(Ra, ny, Pr=0.71, dT=0.02, u_c=0.03, T0=1.0):
 
 
 def rayleigh_benard(nx=256, ny=128, Ra=1e4, Pr=0.71, gamma=1.4, T_bot=1.01, T_top=0.99, u_c=0.03,
-                    seed=1, amp=1e-4, storage="fp32"):
+                    seed=1, amp=1e-4, storage="fp32", fields=True):
     """Rayleigh-Benard convection with gravity as a direct body force (Section V.D).
 
     Periodic in x; walls at y = 0 (hot) and y = ny-1 (cold), at rest.  Velocity walls
@@ -169,6 +169,8 @@ def rayleigh_benard(nx=256, ny=128, Ra=1e4, Pr=0.71, gamma=1.4, T_bot=1.01, T_to
     case["T_scale"] = T_bot - T_top
     case["rho_scale"] = g * (ny - 1) / (case["R"] * T0)  # hydrostatic variation across the layer
     case["T_bot"], case["T_top"] = T_bot, T_top
+    if not fields:
+        return case, None
     rng = np.random.default_rng(seed)
     y = np.arange(ny, dtype=np.float64)
     Tcol = T_bot + (T_top - T_bot) * y / (ny - 1)
@@ -183,13 +185,13 @@ def rayleigh_benard(nx=256, ny=128, Ra=1e4, Pr=0.71, gamma=1.4, T_bot=1.01, T_to
     pert[0, :] = 0.0
     pert[-1, :] = 0.0
     T = T + pert
-    fields = {
+    out = {
         "rho": np.repeat(rho_col[:, None], nx, axis=1).copy(),
         "ux": np.zeros((ny, nx)),
         "uy": np.zeros((ny, nx)),
         "T": T,
     }
-    return case, fields
+    return case, out
 
 
 def shock_tube(nx=4096, ny=4, rho_l=1.05, rho_r=1.0, T=1.0, w1=1.887, storage="fp32"):
@@ -214,7 +216,7 @@ def shock_tube(nx=4096, ny=4, rho_l=1.05, rho_r=1.0, T=1.0, w1=1.887, storage="f
     return case, f
 
 
-def taylor_green(n=64, F0=1e-5, nu=0.02, thermal=False, storage="fp32"):
+def taylor_green(n=64, F0=1e-5, nu=0.02, thermal=False, storage="fp32", fields=True):
     """Steady forced Taylor-Green flow (Section V.A): periodic N x N lattice, node i at
     x = i * 2 pi / N, F = F0 (sin x sin y, cos x cos y), rho = 1 and u = 0 initially,
     w1 = w2 = w3 = w4 (BGK limit).  Closed form u = u0 (sin x sin y, cos x cos y) with
@@ -229,7 +231,7 @@ def taylor_green(n=64, F0=1e-5, nu=0.02, thermal=False, storage="fp32"):
     case["rho_scale"] = case["u0"] ** 2 / (case["R"] * case["T0"])
     b = 2.0 / (case["gamma"] - 1.0)
     case["T_scale"] = case["u0"] ** 2 / (case["R"] * (b + 2.0) / 2.0)
-    return case, uniform_fields(n, n)
+    return case, (uniform_fields(n, n) if fields else None)
 
 
 def taylor_green_fields(n, u0):
@@ -315,11 +317,16 @@ def batched_rb_sweep(count=256, seed=1234, sizes=((64, 32), (128, 64), (256, 128
     return out
 
 
-def serving_trace(duration_s=2.0, rate=200.0, seed=42, scale=1.0, max_nodes=None):
+def serving_trace(duration_s=2.0, rate=200.0, seed=42, scale=1.0, max_nodes=None, steps_choices=(200, 500, 1000, 2000),
+                  steady_frac=0.0, steady_residual=1e-8):
     """Poisson-arriving requests (mean `rate`/s) mixing thermal Couette (32 x 128),
     forced Taylor-Green (256^2 .. 2048^2) and Rayleigh-Benard (128x64 .. 4096x2048,
-    Ra log-uniform up to 1e7, capped at rb_max_resolved_ra of the lattice).  Each request asks for a fixed step count.  `scale` shrinks lattice
-    sides (for small test runs); `max_nodes` caps lattice size."""
+    Ra log-uniform up to 1e7, capped at rb_max_resolved_ra of the lattice).  Each request
+    asks for a fixed step count drawn from `steps_choices`, except a share `steady_frac`
+    of the Couette requests, which ask for the steady state: the residual E_R (Section
+    V.A) below `steady_residual` (those take nu = 0.3, whose slowest shear mode on
+    32 x 128 e-folds in ~5400 steps).  `scale` shrinks lattice sides (for small test
+    runs); `max_nodes` caps lattice size."""
     rng = np.random.default_rng(seed)
     t = 0.0
     reqs = []
@@ -349,17 +356,22 @@ def serving_trace(duration_s=2.0, rate=200.0, seed=42, scale=1.0, max_nodes=None
                 ny //= 2
         if "Ra_drawn" in extra:  # capped at what the (possibly scaled) lattice resolves
             extra["Ra"] = min(extra["Ra_drawn"], rb_max_resolved_ra(ny))
-        steps = int(rng.choice([200, 500, 1000, 2000]))
-        reqs.append({"t_arrival": t, "kind": name, "nx": nx, "ny": ny, "steps": steps, "seed": len(reqs), **extra})
+        steps = int(rng.choice(list(steps_choices)))
+        r = {"t_arrival": t, "kind": name, "nx": nx, "ny": ny, "steps": steps, "seed": len(reqs), **extra}
+        if name == "couette" and steady_frac > 0 and rng.uniform() < 3.0 * steady_frac:
+            r.update(steps=None, residual=steady_residual, nu=0.3)
+        reqs.append(r)
     return reqs
 
 
-def build_request(req, storage="fp16"):
-    """Case and initial fields of one serving request."""
+def build_request(req, storage="fp16", fields=True):
+    """Case and initial fields of one serving request (fields None with fields=False:
+    a long trace builds each request's fields only when it is admitted)."""
     if req["kind"] == "couette":
-        return couette(req["nx"], req["ny"], storage=storage)
+        return couette(req["nx"], req["ny"], nu=req.get("nu", 0.05), storage=storage, fields=fields)
     if req["kind"] == "taylor_green":
         n = req["nx"]
         F0 = 1e-5 * (64.0 / n) ** 2  # keeps u0 at the Section V.A value of 0.026
-        return taylor_green(n, F0=F0, nu=0.02, thermal=True, storage=storage)
-    return rayleigh_benard(req["nx"], req["ny"], Ra=req.get("Ra", 1e4), seed=req["seed"], storage=storage)
+        return taylor_green(n, F0=F0, nu=0.02, thermal=True, storage=storage, fields=fields)
+    return rayleigh_benard(req["nx"], req["ny"], Ra=req.get("Ra", 1e4), seed=req["seed"], storage=storage,
+                           fields=fields)

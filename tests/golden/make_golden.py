@@ -6,6 +6,12 @@ rb_128x64_nusselt.txt: Nusselt number (Section V.D definition, H = ny - 1,
 kappa = nu / Pr, T0 = mean wall temperature) of Rayleigh-Benard convection on a
 128 x 64 lattice, Ra = 1e4, Pr = 0.71, seeded temperature perturbation of amplitude
 1e-2 (seed 1), after 60 000 and 80 000 time steps.
+
+rb_256x128_nusselt.txt: the same on the 256 x 128 lattice of the bench workload
+(perturbation amplitude 1e-4, seed 1, as the workload draws it), every 25 000 steps
+up to 200 000.
+
+    python tests/golden/make_golden.py [rb_128x64] [rb_256x128]
 """
 import os
 import sys
@@ -44,5 +50,24 @@ def rb_128x64():
             fh.write(f"{steps} {nu:.12f}\n")
 
 
+def rb_256x128():
+    case, fields = W.rayleigh_benard(256, 128, Ra=1e4, seed=1)
+    o = oracle.Oracle(case, fields, threads=os.cpu_count())
+    rows = []
+    t0 = time.time()
+    for k in range(8):
+        o.step(25000)
+        rows.append(((k + 1) * 25000, nusselt(case, o.moments())))
+        print(f"  {rows[-1][0]} steps: Nu = {rows[-1][1]:.9f} ({time.time() - t0:.0f} s)", flush=True)
+    with open(os.path.join(HERE, "rb_256x128_nusselt.txt"), "w") as fh:
+        fh.write("# Nusselt number of the FP64 oracle: Rayleigh-Benard 256 x 128, Ra = 1e4, Pr = 0.71,\n")
+        fh.write("# perturbation amplitude 1e-4 (seed 1); written by tests/golden/make_golden.py\n")
+        fh.write("# columns: steps  Nu\n")
+        for steps, nu in rows:
+            fh.write(f"{steps} {nu:.12f}\n")
+
+
 if __name__ == "__main__":
-    rb_128x64()
+    which = sys.argv[1:] or ["rb_128x64", "rb_256x128"]
+    for name in which:
+        globals()[name]()

@@ -107,9 +107,10 @@ def test_fields_after_many_steps(T, name, case, fields):
         assert e[k] <= REL_L2, (name, e)
 
 
-# The thermal Couette flow is the one case held to wider FP32 bounds (tests/parity.py:
-# a moving wall's O(U) populations, rounded by 1-2 ulps per step, integrated by the slow
-# shear mode); at 1000 steps, before that integration, u is held to the common 1e-5.
+# The thermal Couette flow is held to wider FP32 bounds (tests/parity.py: a heating-only
+# temperature signal, and a moving wall's O(U) populations rounded by 1-2 ulps per step
+# and integrated by the slow shear mode); at 1000 steps, before that integration, u is
+# held to the common 1e-5.
 from tests.parity import fp32_bounds  # noqa: E402
 
 

@@ -133,8 +133,14 @@ class Server:
                 if not self.active and not self.retiring:
                     raise MemoryError(f"request {req.rid} needs {need} bytes, more than the whole budget")
                 break  # first come, first served: wait for memory
+            try:
+                lat = tclbm.Lattice(case, None, stream=self.admit_stream.cuda_stream)
+            except tclbm.TclbmError as e:
+                # the free-memory estimate was optimistic (fragmentation): wait for a retirement
+                if e.status != tclbm.ENOMEM or not (self.active or self.retiring):
+                    raise
+                break
             self.queue.popleft()
-            lat = tclbm.Lattice(case, None, stream=self.admit_stream.cuda_stream)
             lat.init_fields(_fields_of(req))  # host fields: synchronises the admission stream only
             lat.set_stream(self.stream.cuda_stream)
             req.t_admit = self._clock()

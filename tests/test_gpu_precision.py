@@ -187,17 +187,19 @@ def _tg_to_steady_state(T, case, fields, residual, check, max_steps):
 
 
 def test_taylor_green_512_to_steady_state_per_format(T):
-    # Taylor-Green on 512^2 (the precision workload's lattice), u0 held at the Section V.A
-    # value (F0 = 1e-5 (64/512)^2, nu = 0.02), started from the closed form: FP32 runs to
-    # E_R < 1e-8 over 1000-step intervals; every format is then compared with the closed
-    # form after the same number of steps.  Second-order convergence puts the FP32 error
-    # at the 64^2 value (1.55e-3, Table 1) times (64/512)^2 = 2.4e-5.  16-bit storage
-    # adds its rounding: round-to-nearest deviations freeze once the per-step change is
-    # below half an ulp, stochastic rounding leaves a noise floor of the residual.
+    # Taylor-Green on 512^2 (the precision workload's lattice) at the Reynolds number of the
+    # Section V.A case (nu = 0.02, u0 = 0.026 * 64 / 512), started from the closed form:
+    # FP32 runs to E_R < 1e-8 over 1000-step intervals and its error against the closed
+    # form is the 64^2 value (1.55e-3, Table 1) times (64/512)^2 = 2.4e-5, second-order
+    # convergence.  Every 16-bit format is compared with the closed form after the same
+    # number of steps.  (With u0 held at 0.026 instead, the 512^2 flow runs at 8 times that
+    # Reynolds number and does not settle: E_R stays near 1e-6 and E2 near 6e-4 for 1.5 M
+    # steps in FP32.)
     n, nu = 512, 0.02
     k = 2 * math.pi / n
-    u0 = 1e-5 * (64.0 / n) ** 2 / (2 * nu * k * k)
-    case, _ = W.taylor_green(n, F0=1e-5 * (64.0 / n) ** 2, nu=nu)
+    u0 = 0.026 * 64.0 / n
+    F0 = 2 * nu * k * k * u0
+    case, _ = W.taylor_green(n, F0=F0, nu=nu)
     ua, va = W.taylor_green_fields(n, u0)
     fields = W.uniform_fields(n, n)
     fields["ux"], fields["uy"] = ua, va
@@ -208,9 +210,9 @@ def test_taylor_green_512_to_steady_state_per_format(T):
     m32, steps, er = _tg_to_steady_state(T, case, fields, 1e-8, 1000, 1_500_000)
     print("fp32 steady at %d steps, E_R %.2e, E2 %.3e" % (steps, er, e2(m32)))
     assert er < 1e-8
-    assert 1.0e-5 < e2(m32) < 5e-5
-    bound = {("fp16", "nearest"): 3e-3, ("fp16", "stochastic"): 3e-3, ("bf16", "nearest"): 3e-2,
-             ("bf16", "stochastic"): 3e-2}
+    assert 1.2e-5 < e2(m32) < 4.8e-5  # 2.4e-5 within a factor 2
+    bound = {("fp16", "nearest"): 2e-2, ("fp16", "stochastic"): 2e-2, ("bf16", "nearest"): 2e-1,
+             ("bf16", "stochastic"): 2e-1}
     for (storage, rounding), b in bound.items():
         m, _, er16 = _tg_to_steady_state(T, dict(case, storage=storage, rounding=rounding), fields, 1e-8, 1000, steps)
         print("%s %s after %d steps: E_R %.2e, E2 %.3e" % (storage, rounding, steps, er16, e2(m)))
@@ -249,8 +251,10 @@ def test_rayleigh_benard_256x128_nusselt_history(T, storage, rounding, bound):
         d = lat.diagnostics()
         nu = 1.0 + d[5] / n * H / (kappa * dT)
         print(storage, rounding, steps, "Nu %.5f (FP64 %.5f)" % (nu, gold[steps]))
-        if steps <= 50000:
+        if storage == "fp32" and steps <= 50000:
             assert abs(nu - 1.0) < 1e-3 and abs(gold[steps] - 1.0) < 1e-3
-        elif steps >= 150000:
+        elif steps >= (150000 if storage == "fp32" else 175000):
+            # 16-bit stochastic rounding seeds the convective mode with its own noise, so
+            # convection sets in earlier; the developed flow is compared
             assert abs(nu / gold[steps] - 1.0) < bound
     lat.close()

@@ -194,6 +194,22 @@ def rayleigh_benard(nx=256, ny=128, Ra=1e4, Pr=0.71, gamma=1.4, T_bot=1.01, T_to
     return case, out
 
 
+def rb_onset(Ra, nx=200, ny=100, dT=0.06, u_c=0.005, amp=1e-2, storage="fp32"):
+    """Rayleigh-Benard layer for the onset of convection (Section V.D: the 200 x 100 mesh
+    and the 6 % temperature difference of the paper): u_c = 0.005 keeps the layer weakly
+    stratified (g H / (R T0) = 2.5e-3) with w1 <= 1.8 near Ra = 1708, and the start is the
+    linear conduction profile plus the shape of the critical mode,
+    T' = amp dT sin(pi y / H) cos(2 pi x / nx) (one wavelength across nx = 2 H, wave number
+    close to the critical 3.117 / H)."""
+    case, fields = rayleigh_benard(nx, ny, Ra=Ra, T_bot=1.0 + dT / 2, T_top=1.0 - dT / 2, u_c=u_c, seed=0, amp=0.0,
+                                   storage=storage)
+    y = np.arange(ny)[:, None]
+    x = np.arange(nx)[None, :]
+    fields["T"] = fields["T"] + amp * dT * np.sin(np.pi * y / (ny - 1)) * np.cos(2 * np.pi * x / nx)
+    case["name"] = f"rb_onset_{nx}x{ny}_Ra{Ra:g}"
+    return case, fields
+
+
 def shock_tube(nx=4096, ny=4, rho_l=1.05, rho_r=1.0, T=1.0, w1=1.887, storage="fp32"):
     """Low-Mach shock tube (Section V.C): periodic in y, equilibrium distributions at
     x = 0 and x = nx-1 with the initial end states; gamma = 1.4, Pr = 0.71,

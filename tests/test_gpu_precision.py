@@ -187,18 +187,21 @@ def _tg_to_steady_state(T, case, fields, residual, check, max_steps):
 
 
 def test_taylor_green_512_per_format(T):
-    # Taylor-Green on 512^2 (the precision workload: u0 held at the Section V.A value of
-    # 0.026, F0 = 1e-5 (64/512)^2, nu = 0.02), started from the closed form and run for
-    # 10^6 steps (3 e-foldings of the slowest mode), E2 against the closed form and the
-    # residual E_R (1000-step interval) of every stored format.  FP32 does not reach
-    # E_R < 1e-8 here: its roundings (about an ulp of the population deviations per step,
-    # partly systematic) are integrated by the slow mode (e-folding 1/(nu k^2) = 332 000
-    # steps) into an absolute velocity error of ~1e-5 and a residual floor near 1e-6
-    # (measured: E2 6.4e-4, E_R 4.5e-7 at 10^6 steps; the same ~1e-5 absolute error at an
-    # 8 times smaller u0), the mechanism of the thermal Couette bound.
+    # Taylor-Green on 512^2 at the Reynolds number of the Section V.A case (nu = 0.02,
+    # u0 = 0.026 * 64 / 512 = 3.25e-3), started from the closed form and run for 10^6 steps
+    # (3 e-foldings of the slowest mode, 1/(nu k^2) = 332 000 steps): E2 against the closed
+    # form and the residual E_R (1000-step interval) of every stored format.  Measured:
+    # FP32 2.26e-3 (E_R 2.2e-7), FP16 nearest 9.7e-3, FP16 stochastic 3.2e-3, BF16 nearest
+    # 0.35, BF16 stochastic 1.05e-2.  FP32 settles but not to the closed form's second-order
+    # error (2.4e-5): its roundings, partly systematic, are integrated by the slow mode into
+    # an absolute velocity error of ~7e-6, and its residual floor is 2e-7, above 1e-8.
+    # Round-to-nearest BF16 cannot follow the slow relaxation at all.  (With u0 held at
+    # 0.026 instead, the 512^2 flow runs at 8 times that Reynolds number and is unstable:
+    # a 1e-3 perturbation grows to O(1) within 500 000 steps.)
     n, nu, steps = 512, 0.02, 1_000_000
-    case, _ = W.taylor_green(n, F0=1e-5 * (64.0 / n) ** 2, nu=nu)
-    u0 = case["u0"]
+    k = 2 * math.pi / n
+    u0 = 0.026 * 64.0 / n
+    case, _ = W.taylor_green(n, F0=2 * nu * k * k * u0, nu=nu)
     ua, va = W.taylor_green_fields(n, u0)
     fields = W.uniform_fields(n, n)
     fields["ux"], fields["uy"] = ua, va
@@ -206,8 +209,8 @@ def test_taylor_green_512_per_format(T):
     def e2(m):
         return math.sqrt(np.sum((m["ux"] - ua) ** 2 + (m["uy"] - va) ** 2) / np.sum(ua ** 2 + va ** 2))
 
-    bound = {("fp32", "nearest"): (1.5e-3, 1e-5), ("fp16", "nearest"): (3e-2, 1.0),
-             ("fp16", "stochastic"): (3e-2, 1.0), ("bf16", "nearest"): (3e-1, 1.0), ("bf16", "stochastic"): (3e-1, 1.0)}
+    bound = {("fp32", "nearest"): (5e-3, 1e-6), ("fp16", "nearest"): (2e-2, 3e-3),
+             ("fp16", "stochastic"): (7e-3, 3e-3), ("bf16", "nearest"): (0.7, 0.1), ("bf16", "stochastic"): (2.5e-2, 3e-2)}
     for (storage, rounding), (b_e2, b_er) in bound.items():
         lat = T.Lattice(dict(case, storage=storage, rounding=rounding), fields)
         lat.step(steps - 1000)

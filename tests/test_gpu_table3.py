@@ -1,18 +1,20 @@
 """Rayleigh-Benard convection against Table 3 of Section V.D (Nusselt number versus Ra,
-Pr = 0.71, aspect ratio 2:1, the paper's meshes: Ny = 80 below Ra = 1e4).
+Pr = 0.71, aspect ratio 2:1, the paper's meshes: N_y = 80 below Ra = 1e4, 100 up to 3e4,
+150 at 5e4).
 
-The run goes to a steady state (Nu changing by less than 2e-4 relative over 80,000
-steps).  Measured on a GB300 (FP32): Ra = 2500 gives 1.482 against the reference 1.475
-(+0.5 %) and the paper's 1.468; Ra = 5000 gives 2.065 against 2.116 (-2.4 %).  At higher
-Ra the gap grows (Ra = 1e4: -5.4 %, 3e4: -9.8 %, 5e4: -11.4 % on the paper's meshes):
-with this build's readings of the paper -- total-energy h with no work term for the body
-force, and a layer stratified by gH / RT0 = 0.27 -- the convection departs from the
-Boussinesq reference as it strengthens.  The test pins the two low-Ra rows and the
-ordering of the others.
+Set-up (workloads.rb_table3): the paper's 6 % temperature difference and the smallest
+characteristic velocity that keeps w1 at 1.78, a weakly stratified layer (g H / (R T0)
+between 0.006 and 0.05).  The run goes to a steady state (Nu changing by less than 2e-4
+relative over 80,000 steps).  Measured on a GB300 (FP32): 1.4657 / 2.0969 / 2.6378 /
+3.6010 / 4.1453 at Ra = 2500 / 5000 / 1e4 / 3e4 / 5e4, against the paper's 1.468 / 2.106
+/ 2.650 / 3.629 / 4.181 (0.15-0.85 % below) and the reference column 1.475 / 2.116 /
+2.661 / 3.662 / 4.245 (0.6-2.3 % below).  With the bench workload's stratification
+(u_c = 0.03 at 2 % temperature difference, g H / c_p four times Delta T) the high-Ra rows
+fall 5-11 % below the reference: the total-energy equation without a work term of the
+body force departs from the Boussinesq reference when the layer is that stratified.
 """
 import os
 
-import numpy as np
 import pytest
 
 from paper_1610_07114_gb300 import workloads as W
@@ -45,32 +47,27 @@ def table3():
     return rows
 
 
-def steady_nusselt(T, Ra, ny):
-    nx = 2 * ny
-    case, fields = W.rayleigh_benard(nx, ny, Ra=Ra, seed=3, amp=1e-2)
+def steady_nusselt(T, Ra):
+    case, fields = W.rb_table3(Ra)
+    nx, ny = case["nx"], case["ny"]
     lat = T.Lattice(case, fields)
     H, kappa, dT = ny - 1, case["visc"] / case["Pr"], case["T_bot"] - case["T_top"]
     hist = []
-    for _ in range(100):
+    for _ in range(150):
         lat.step(20000)
         d = lat.diagnostics()
         hist.append(1.0 + d[5] / (nx * ny) * H / (kappa * dT))
         if len(hist) > 5 and abs(hist[-1] - hist[-5]) < 2e-4 * abs(hist[-1]) and hist[-1] > 1.01:
             break
     lat.close()
-    assert len(hist) < 100, "no steady state"
+    assert len(hist) < 150, "no steady state"
     return hist[-1]
 
 
-@pytest.mark.parametrize("Ra,ny,tol", [(2500, 80, 0.01), (5000, 80, 0.03)])
-def test_nusselt_matches_table3(T, Ra, ny, tol):
-    nu = steady_nusselt(T, Ra, ny)
+@pytest.mark.parametrize("Ra", [2500, 5000, 10000, 30000, 50000])
+def test_nusselt_matches_table3(T, Ra):
+    nu = steady_nusselt(T, Ra)
     nu_paper, nu_ref = table3()[Ra]
     print(Ra, "Nu %.4f (paper %.3f, reference %.3f)" % (nu, nu_paper, nu_ref))
-    assert abs(nu / nu_ref - 1.0) < tol
-
-
-def test_nusselt_grows_with_rayleigh_number(T):
-    nus = [steady_nusselt(T, Ra, ny) for Ra, ny in ((2500, 80), (10000, 100), (30000, 100))]
-    print("Nu", nus)
-    assert np.all(np.diff(nus) > 0.3)
+    assert abs(nu / nu_paper - 1.0) < 0.01
+    assert abs(nu / nu_ref - 1.0) < 0.03

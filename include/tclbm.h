@@ -107,6 +107,10 @@ typedef struct {
     int32_t storage;      /* TCLBM_STORE_* */
     double T_ref;         /* reference temperature of the Nusselt sum in diagnostics */
     int32_t rounding;     /* 16-bit storage: TCLBM_ROUND_NEAREST or TCLBM_ROUND_STOCHASTIC */
+    int32_t work;         /* 1: the body force's power F.u is a source of total energy (thermal only;
+                             an extension, the paper's Eq. 22 has no force term): the h update
+                             gains (1 - w_h/2) W_a F.u (D2Q9 weights W_a) and the energy moment
+                             is rho E = sum h_bar + F.u / 2; 0: paper-literal */
 } tclbm_params;
 
 /* Device allocator hooks.  alloc(bytes, stream, ctx) returns device memory or NULL;

@@ -49,6 +49,7 @@ class OracleParams(ctypes.Structure):
         ("wall_kind", ctypes.c_int32 * 4), ("wall_therm", ctypes.c_int32 * 4),
         ("wall_rho", ctypes.c_double * 4), ("wall_ux", ctypes.c_double * 4),
         ("wall_uy", ctypes.c_double * 4), ("wall_T", ctypes.c_double * 4),
+        ("work", ctypes.c_int32),
     ]
 
 
@@ -118,6 +119,7 @@ def params(case: dict) -> OracleParams:
         p.wall_kind[i] = WALL[w["kind"]]
         p.wall_therm[i] = THERM[w.get("therm", "fixed")]
         p.wall_rho[i], p.wall_ux[i], p.wall_uy[i], p.wall_T[i] = w["rho"], w["ux"], w["uy"], w["T"]
+    p.work = 1 if case.get("work") else 0
     if case.get("w_equal"):
         # BGK limit of Section V.A: w2 = w3 = w4 = w1 with w1 fixed from the viscosity.
         if case["visc_law"] != "nu":

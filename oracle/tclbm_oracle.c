@@ -45,6 +45,11 @@
  *     1/tau_hf = (Pr - 1)/(mu/p + 1/2) = (Pr - 1) w1 (finite at Pr = 1).
  *   - Initial state: f_bar = f^eq - S/2 (C = 0 at t = 0), h_bar = h^eq, so that
  *     Eq. 20 returns the prescribed fields.
+ *   - Optional work term (not in the paper, whose total-energy equation Eq. 22 has no
+ *     force term): the power of the body force F.u enters the h update as a source
+ *     q_a = W_a F.u (D2Q9 weights, zeroth moment F.u, first moment zero) with the factor
+ *     (1 - w_h/2), and the energy moment carries half a step of it, rho E =
+ *     sum h_bar + F.u / 2, as Eq. 20 does for the momentum.  Initial h_bar = h^eq - q/2.
  *   - Walls are "wet": the wall lies on the first/last node row (or column); the
  *     boundary scheme rebuilds that node's populations after streaming and the
  *     node then collides like any other.  Zou-He is written for transformed
@@ -66,6 +71,9 @@
  * e_a = sqrt(2) (cos((a-9/2)pi/2), sin((a-9/2)pi/2)) for a = 5..8; c = 1. */
 static const int EX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int EY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+/* D2Q9 weights (zeroth moment 1, first moment 0): the shape of the work source. */
+static const double WQ[Q] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 
 enum { SIDE_XM = 0, SIDE_XP = 1, SIDE_YM = 2, SIDE_YP = 3 };
 enum { WALL_PERIODIC = 0, WALL_ZOUHE = 1, WALL_NEE = 2, WALL_EQUILIBRIUM = 3 };
@@ -91,6 +99,8 @@ typedef struct {
     int32_t wall_kind[4];   /* per side x-, x+, y-, y+ : WALL_* */
     int32_t wall_therm[4];  /* THERM_* for the h populations of a wall */
     double wall_rho[4], wall_ux[4], wall_uy[4], wall_T[4];
+    int32_t work;        /* 1: the body force's power F.u as a source of total energy (an extension:
+                            the paper's Eq. 22 has none) */
 } oracle_params;
 
 typedef struct { double rho, ux, uy, T, Fx, Fy, ax, ay; } macro_t;
@@ -213,6 +223,7 @@ static void macro_of(const oracle_params* p, const double fb[9], const double hb
     if (p->thermal) {
         double sh = 0.0;
         for (int a = 0; a < Q; ++a) sh += hb[a];
+        if (p->work) sh += 0.5 * (Fx * m->ux + Fy * m->uy); /* rho E = sum h_bar + F.u / 2 */
         m->T = 2.0 / (b_dof(p) * p->R) * (sh / rho - 0.5 * (m->ux * m->ux + m->uy * m->uy));
     } else {
         m->T = p->T0;
@@ -345,10 +356,11 @@ static void collide(const oracle_params* p, const double fb[9], const double hb[
     double feq[9], heq[9];
     oracle_feq(rho, ux, uy, RT, feq);
     oracle_heq(rho, ux, uy, RT, b, heq);
+    const double qw = p->work ? m->Fx * ux + m->Fy * uy : 0.0;   /* power of the body force */
     for (int a = 0; a < Q; ++a) {
         const double Z = EX[a] * ux + EY[a] * uy - 0.5 * uu;           /* Eq. 22 */
         const double K = Z * inv_tau_hf * (fb[a] - feq[a] + 0.5 * S[a] + 0.5 * C[a]);
-        hout[a] = hb[a] - wh * (hb[a] - heq[a]) + (1.0 - 0.5 * wh) * K;
+        hout[a] = hb[a] - wh * (hb[a] - heq[a]) + (1.0 - 0.5 * wh) * (K + WQ[a] * qw);
     }
 }
 
@@ -443,6 +455,13 @@ static void wall_rebuild(const oracle_params* p, int side, int x, int y, double 
     if (!p->thermal) return;
     if (kind == WALL_EQUILIBRIUM) {
         oracle_heq(p->wall_rho[side], uwx, uwy, p->R * p->wall_T[side], b, hb);
+        if (p->work) {
+            const double rw = p->wall_rho[side];
+            double Fx = 0.0, Fy = 0.0;
+            if (p->force_kind == FORCE_UNIFORM_ACCEL) { Fx = rw * p->ax; Fy = rw * p->ay; }
+            else if (p->force_kind == FORCE_TAYLOR_GREEN) force_field(p, x, y, &Fx, &Fy);
+            for (int a = 0; a < Q; ++a) hb[a] -= 0.5 * WQ[a] * (Fx * uwx + Fy * uwy);
+        }
         return;
     }
     /* Temperature by non-equilibrium extrapolation: h_b = h^eq(rho_b, u_b, T_w) + [h_f - h^eq(rho_f, u_f, T_f)],
@@ -452,6 +471,10 @@ static void wall_rebuild(const oracle_params* p, int side, int x, int y, double 
     double eqw[9], eqf[9];
     oracle_heq(mb.rho, mb.ux, mb.uy, p->R * Tw, b, eqw);
     oracle_heq(mf.rho, mf.ux, mf.uy, p->R * mf.T, b, eqf);
+    if (p->work) { /* the transformed equilibria h^eq - q/2 of both nodes */
+        const double qb = mb.Fx * mb.ux + mb.Fy * mb.uy, qf = mf.Fx * mf.ux + mf.Fy * mf.uy;
+        for (int a = 0; a < Q; ++a) { eqw[a] -= 0.5 * WQ[a] * qb; eqf[a] -= 0.5 * WQ[a] * qf; }
+    }
     for (int a = 0; a < Q; ++a) hb[a] = eqw[a] + (hf[a] - eqf[a]);
 }
 
@@ -478,6 +501,7 @@ int oracle_check(const oracle_params* p) {
     if (!x_periodic(p) && p->nx < 3) return -1;
     if (!y_periodic(p) && p->ny < 3) return -1;
     if (p->gamma <= 1.0 || p->Pr <= 0.0 || p->R <= 0.0 || p->T0 <= 0.0) return -1;
+    if (p->work && !p->thermal) return -1;
     return 0;
 }
 
@@ -517,7 +541,8 @@ int oracle_init(const oracle_params* p, const double* rho, const double* ux, con
             for (int a = 0; a < Q; ++a) f[at(p, a, x, y)] = feq[a] - 0.5 * S[a];
             if (p->thermal) {
                 oracle_heq(rho[i], ux[i], uy[i], p->R * Tn, b, heq);
-                for (int a = 0; a < Q; ++a) h[at(p, a, x, y)] = heq[a];
+                const double qw = p->work ? Fx * ux[i] + Fy * uy[i] : 0.0;
+                for (int a = 0; a < Q; ++a) h[at(p, a, x, y)] = heq[a] - 0.5 * WQ[a] * qw;
             }
         }
     for (int y = 0; y < p->ny; ++y)
@@ -659,6 +684,7 @@ void oracle_collide_node(const oracle_params* p, const double fb[9], const doubl
     if (p->thermal) {
         double sh = 0.0;
         for (int a = 0; a < Q; ++a) sh += hb[a];
+        if (p->work) sh += 0.5 * (Fx * m.ux + Fy * m.uy);
         m.T = 2.0 / (b_dof(p) * p->R) * (sh / rho - 0.5 * (m.ux * m.ux + m.uy * m.uy));
     } else m.T = p->T0;
     double hzero[9] = {0};

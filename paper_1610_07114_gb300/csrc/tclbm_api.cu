@@ -98,6 +98,7 @@ tclbm_status validate(const tclbm_params* p) {
     if (p->force_kind < TCLBM_FORCE_NONE || p->force_kind > TCLBM_FORCE_TAYLOR_GREEN)
         return fail(TCLBM_EINVAL, "bad force_kind");
     if (p->correction && !p->thermal) return fail(TCLBM_EINVAL, "the correction term needs thermal = 1");
+    if (p->work && !p->thermal) return fail(TCLBM_EINVAL, "the work term needs thermal = 1");
     if (p->storage < TCLBM_STORE_FP32 || p->storage > TCLBM_STORE_FP16) return fail(TCLBM_EINVAL, "bad storage");
     if (p->rounding != TCLBM_ROUND_NEAREST && p->rounding != TCLBM_ROUND_STOCHASTIC)
         return fail(TCLBM_EINVAL, "bad rounding");
@@ -161,6 +162,7 @@ void derive(tclbm_lattice* L) {
     }
     d.dRTp = (float)(p.R * p.T0 - RTb);
     d.inv_bR2 = 2.0 / (b * p.R);  // the same FP64 expression tclbm_diagnostics_noalloc() takes
+    d.work = p.thermal && p.work;
     d.T0d = p.T0;
     // rest-state populations f^eq(1, 0, RT0), h^eq(1, 0, RT0) with Et = Et0
     const double x0 = 1.0 - RTb, x1 = 0.5 * RTb;
@@ -276,6 +278,8 @@ __global__ void init_kernel(const DevParams p, const double* __restrict__ rho, c
                     hv = 0.5 * r * (A * (ex[q] * vx + ey[q] * vy) + B * (ex[q] * ex[q] * ux2 + ey[q] * ey[q] * uy2) + C);
                 else
                     hv = 0.25 * r * B * ex[q] * ey[q] * vx * vy;
+                if (p.work)  // h_bar = h^eq - q / 2, q_a = W_a F.u
+                    hv -= 0.5 * (q == 0 ? 4.0 / 9.0 : (q <= 4 ? 1.0 / 9.0 : 1.0 / 36.0)) * (Fx * vx + Fy * vy);
             }
             int xs = x - ex[q], ys = y - ey[q];
             if (p.xper) xs = wrapi(xs, p.nx); else if (xs < 0 || xs >= p.nx) continue;
@@ -350,7 +354,8 @@ __device__ __forceinline__ void node_fields(const DevParams& p, const ST* __rest
     sh = 0;
     if (THERMAL) {
         for (int q = 0; q < 9; ++q) sh += (double)p.hbase[q] + hv[q];
-        T = p.inv_bR2 * (sh / r - 0.5 * (vx * vx + vy * vy));
+        const double she = p.work ? sh + 0.5 * (Fx * vx + Fy * vy) : sh;  // rho E with the work term
+        T = p.inv_bR2 * (she / r - 0.5 * (vx * vx + vy * vy));
     } else {
         T = p.T0d;
     }

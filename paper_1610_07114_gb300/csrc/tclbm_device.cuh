@@ -60,7 +60,11 @@ struct DevParams {
     // FP64 constants of the field conversions (moments, diagnostics): T = inv_bR2 (E - u^2/2)
     // with inv_bR2 = 2 / (b R), and T0, as the FP64 initialisation uses them
     double inv_bR2, T0d;
+    int work;  // 1: the body force's power F.u is a source of total energy (rho E = sum h_bar + F.u/2)
 };
+
+// D2Q9 weights: the shape of the work source (zeroth moment 1, first moment 0).
+constexpr float kW0 = 4.0f / 9.0f, kW1 = 1.0f / 9.0f, kW5 = 1.0f / 36.0f;
 
 // Counter-based 32-bit mix of (node, pair, step): random bits for stochastic rounding.
 __device__ __forceinline__ uint32_t sr_bits(uint32_t node, uint32_t pair, uint32_t step) {
@@ -183,7 +187,9 @@ __device__ __forceinline__ Macro macro_of(const DevParams& p, const float* f, co
     m.ax = __fmul_rn(Fx, irho);
     m.ay = __fmul_rn(Fy, irho);
     if (THERMAL) {
-        const float sdh = sum9(h);
+        float sdh = sum9(h);
+        // with the work term, rho E = sum h_bar + F.u / 2
+        if (p.work) sdh = __fmaf_rn(0.5f, __fmaf_rn(Fx, m.ux, __fmul_rn(Fy, m.uy)), sdh);
         m.dEt = __fmul_rn(__fmaf_rn(-p.Et0, m.drho, sdh), irho);
         m.Et = __fadd_rn(p.Et0, m.dEt);
         const float ke = __fmul_rn(0.5f, __fmaf_rn(m.ux, m.ux, __fmul_rn(m.uy, m.uy)));
@@ -437,6 +443,13 @@ __device__ __forceinline__ void collide(const DevParams& p, const float* f, cons
             ho[2 * k + 1] = r.x;
             ho[2 * k + 2] = r.y;
         }
+        if (p.work) {
+            // the power of the body force, (1 - w_h / 2) W_a F.u
+            const float cq = (1.0f - 0.5f * wh) * (rho * (ax * ux + ay * uy));
+            ho[0] += kW0 * cq;
+#pragma unroll
+            for (int q = 1; q < 9; ++q) ho[q] += (q < 5 ? kW1 : kW5) * cq;
+        }
     }
 }
 
@@ -537,6 +550,13 @@ __device__ __forceinline__ void wall_rebuild_side(const DevParams& p, int x, int
         const float Ete = 0.5f * (p.b * RTe + uwx * uwx + uwy * uwy);
         const float dEte = 0.5f * p.b * dRTe + 0.5f * (uwx * uwx + uwy * uwy) + (0.5f * p.b * p.RT0 - p.Et0);
         dheq(p, rw, rw - 1.0f, uwx, uwy, RTe, dRTe, Ete, dEte, h);
+        if (p.work) {  // h_bar^eq = h^eq - q / 2 at the wall state
+            float Fx, Fy;
+            force_at(p, x, y, rw, Fx, Fy);
+            const float hq = 0.5f * (Fx * uwx + Fy * uwy);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) h[q] -= (q == 0 ? kW0 : (q < 5 ? kW1 : kW5)) * hq;
+        }
         return;
     }
     // temperature by non-equilibrium extrapolation around the rebuilt node's rho and u:
@@ -548,6 +568,18 @@ __device__ __forceinline__ void wall_rebuild_side(const DevParams& p, int x, int
     float ew[9], ef[9];
     dheq(p, mb.rho, mb.drho, mb.ux, mb.uy, RTw, dRTw, Etw, dEtw, ew);
     dheq(p, mf.rho, mf.drho, mf.ux, mf.uy, mf.RT, mf.dRT, mf.Et, mf.dEt, ef);
+    if (p.work) {  // the transformed equilibria h^eq - q / 2 of both nodes
+        float Fbx, Fby, Ffx, Ffy;
+        force_at(p, x, y, mb.rho, Fbx, Fby);
+        force_at(p, x + S::nxv, y + S::nyv, mf.rho, Ffx, Ffy);
+        const float hqb = 0.5f * (Fbx * mb.ux + Fby * mb.uy), hqf = 0.5f * (Ffx * mf.ux + Ffy * mf.uy);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const float w = q == 0 ? kW0 : (q < 5 ? kW1 : kW5);
+            ew[q] -= w * hqb;
+            ef[q] -= w * hqf;
+        }
+    }
 #pragma unroll
     for (int q = 0; q < 9; ++q) h[q] = hf[q] + (ew[q] - ef[q]);
 }

@@ -62,7 +62,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 __global__ void __launch_bounds__(kBlock) noalloc_sums(const double* __restrict__ f, const double* __restrict__ h,
                                                        const double* __restrict__ usnap, long long n, int nx, int ny,
                                                        int thermal, int force_kind, double ax, double ay, double famp,
-                                                       double bR, double T0, double T_ref, double* partial) {
+                                                       double bR, double T0, double T_ref, int work, double* partial) {
     __shared__ double red[kBlock / 32][TCLBM_NDIAG];
     double acc[TCLBM_NDIAG] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(kBlock) noalloc_sums(const double* __restrict_
             Fy = famp * (double)(float)cos(ax_) * (double)(float)cos(ay_);
         }
         const double vx = (jx + 0.5 * Fx) / r, vy = (jy + 0.5 * Fy) / r;
-        const double T = thermal ? 2.0 / bR * (sh / r - 0.5 * (vx * vx + vy * vy)) : T0;
+        const double she = work ? sh + 0.5 * (Fx * vx + Fy * vy) : sh;  // rho E with the work term
+        const double T = thermal ? 2.0 / bR * (she / r - 0.5 * (vx * vx + vy * vy)) : T0;
         acc[0] += r;
         acc[1] += r * vx;
         acc[2] += r * vy;
@@ -170,7 +171,7 @@ extern "C" tclbm_status tclbm_diagnostics_noalloc(const tclbm_params* params, co
     noalloc_sums<<<(int)nb, kBlock, 0, s>>>(f, params->thermal ? h : nullptr, u_snap, n, params->nx, params->ny,
                                            params->thermal, params->force_kind, (double)(float)params->ax,
                                            (double)(float)params->ay, (double)(float)params->famp, bR,
-                                           params->T0, params->T_ref, scratch);
+                                           params->T0, params->T_ref, params->thermal && params->work, scratch);
     noalloc_finish<<<1, 32, 0, s>>>(scratch, (int)nb, out_on_device ? out : result);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && !out_on_device)

@@ -56,6 +56,7 @@ class tclbm_params(ctypes.Structure):
         ("storage", ctypes.c_int32),
         ("T_ref", ctypes.c_double),
         ("rounding", ctypes.c_int32),
+        ("work", ctypes.c_int32),
     ]
 
 
@@ -307,6 +308,7 @@ def params_from_case(case: dict) -> tclbm_params:
     p.storage = STORAGE[case.get("storage", "fp32")]
     p.T_ref = case.get("T_ref", case["T0"])
     p.rounding = ROUNDING[case.get("rounding", "nearest")]
+    p.work = int(bool(case.get("work")))
     return p
 
 

@@ -20,6 +20,8 @@ Case dict vocabulary (names follow the paper's notation):
                       {"kind": "taylor_green", "amp"}: F = amp (sin kx sin ky, cos kx cos ky)
     walls             {"x-","x+","y-","y+"} -> {"kind": "periodic"|"zouhe"|"nee"|"equilibrium",
                       "ux", "uy", "T", "rho", "therm": "fixed"|"adiabatic"}
+    work              True: the body force's power F.u enters the total energy (an extension;
+                      the paper's Eq. 22 has no force term)
     storage           "fp32" | "bf16" | "fp16" population storage of the CUDA path
     U_ref, rho_scale, T_scale
                       the case's own scales of velocity, density variation and temperature

@@ -9,7 +9,7 @@ kappa = nu / Pr, T0 = mean wall temperature) of Rayleigh-Benard convection on a
 
 rb_256x128_nusselt.txt: the same on the 256 x 128 lattice of the bench workload
 (perturbation amplitude 1e-4, seed 1, as the workload draws it), every 25 000 steps
-up to 200 000.
+up to 300 000.
 
     python tests/golden/make_golden.py [rb_128x64] [rb_256x128]
 """
@@ -55,7 +55,7 @@ def rb_256x128():
     o = oracle.Oracle(case, fields, threads=os.cpu_count())
     rows = []
     t0 = time.time()
-    for k in range(8):
+    for k in range(12):
         o.step(25000)
         rows.append(((k + 1) * 25000, nusselt(case, o.moments())))
         print(f"  {rows[-1][0]} steps: Nu = {rows[-1][1]:.9f} ({time.time() - t0:.0f} s)", flush=True)

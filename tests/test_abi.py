@@ -48,6 +48,7 @@ def _valid_case():
     (lambda c: c.update(Pr=0.0), -1),
     (lambda c: c.update(w2=2.5), -1),
     (lambda c: c.update(thermal=False), -1),  # correction without thermal
+    (lambda c: c.update(thermal=False, correction=False, work=True), -1),  # work term without thermal
     (lambda c: c["walls"]["y+"].update(kind="periodic"), -1),  # one side periodic, its opposite a wall
     (lambda c: [c["walls"][s].update(kind="nee") for s in ("x-", "x+")], -6),  # walls on both axes
     (lambda c: c.update(ny=2), -1),  # walled axis too short

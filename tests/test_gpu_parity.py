@@ -403,3 +403,36 @@ def test_tile_kernel_refuses_lattices_it_cannot_serve(T):
         athermal.set_kernel(2)
     lat.close()
     athermal.close()
+
+
+WORK_CASES = [
+    ("periodic_accel", lambda: W.random_periodic(70, 37, seed=61, force="accel")),
+    ("periodic_tg", lambda: W.random_periodic(45, 33, seed=62, force="taylor_green")),
+    ("rb_zouhe_nee", lambda: W.rayleigh_benard(96, 48, Ra=1e4, seed=63, amp=1e-2)),
+    ("ywalls_nee", lambda: W.with_walls(*W.random_periodic(53, 41, seed=64, force="accel"), axis="y", kind="nee")),
+    ("xwalls_eq", lambda: W.with_walls(*W.random_periodic(67, 9, seed=65, force="accel"), axis="x",
+                                       kind="equilibrium")),
+]
+
+
+@pytest.mark.parametrize("name,make", WORK_CASES, ids=[c[0] for c in WORK_CASES])
+def test_work_term_matches_oracle(T, name, make):
+    # the body force's power as a source of total energy (tclbm_params.work, an extension of
+    # Eq. 22): every kernel variant against the FP64 oracle at the FP32 parity bar
+    case, fields = make()
+    case = dict(case, work=True)
+    o = oracle.Oracle(case, fields, threads=8)
+    o.step(300)
+    om = o.moments()
+    for kernel in (2, 1, 0):
+        lat = T.Lattice(case, fields)
+        try:
+            lat.set_kernel(kernel)
+        except T.TclbmError:
+            lat.close()
+            continue
+        lat.step(300)
+        e = field_errors(lat.moments(), om, case)
+        lat.close()
+        print(name, kernel, e)
+        assert e["rho"] <= REL_L2 and e["u"] <= REL_L2 and e["T"] <= REL_L2, (name, kernel, e)

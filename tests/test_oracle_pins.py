@@ -441,6 +441,62 @@ def test_temperature_wave_decays_at_thermal_diffusivity():
     assert kappa == pytest.approx(nu / Pr, rel=2e-2)
 
 
+@pytest.mark.parametrize("work", [False, True])
+def test_uniformly_accelerated_gas_and_the_work_term(work):
+    # A periodic gas at rest under a uniform acceleration a: u grows by exactly a per step
+    # (Eq. 20), so the kinetic energy grows by F (u_n + u_n+1) / 2 per step.  The paper's
+    # total-energy equation (Eq. 22) has no work term: the total energy stays constant and
+    # the temperature falls by u^2 / (b R).  With the work term (an option of this build)
+    # the total energy grows by the force's power and the gas keeps its temperature.
+    n, a, steps = 4, 2e-4, 400
+    case = W.base_case(n, n, force={"kind": "accel", "ax": a, "ay": 0.0}, work=work)
+    o = oracle.Oracle(case, W.uniform_fields(n, n))
+    o.step(steps)
+    m = o.moments()
+    b = 2.0 / (case["gamma"] - 1.0)
+    u = a * steps
+    np.testing.assert_allclose(m["ux"], u, rtol=1e-10)
+    expect_T = 1.0 if work else 1.0 - u * u / (b * case["R"])
+    np.testing.assert_allclose(m["T"], expect_T, rtol=0, atol=1e-12)
+    assert work or 1.0 - m["T"].max() > 1e-4  # the cooling the test tells apart
+
+
+@pytest.mark.parametrize("force", ["accel", "taylor_green"])
+def test_initial_state_returns_the_prescribed_fields_with_the_work_term(force):
+    # The initial populations (f_bar = f^eq - S/2, h_bar = h^eq - q/2) give back the
+    # prescribed rho, u and T through Eq. 20 and the energy moment rho E = sum h_bar + F.u/2.
+    case, fields = W.random_periodic(12, 10, seed=5, force=force)
+    case["work"] = True
+    m = oracle.Oracle(case, fields).moments()
+    for k in ("rho", "ux", "uy", "T"):
+        np.testing.assert_allclose(m[k], fields[k], rtol=0, atol=1e-14)
+
+
+def test_work_term_energy_budget_on_a_periodic_column():
+    # With the work term the total energy of a periodic lattice (nothing crosses a
+    # boundary) changes each step by the power of the force, sum F.u, averaged over the
+    # step's two ends (the half-step shift of the energy moment): a random state under
+    # gravity, step by step.
+    n = 6
+    case = W.base_case(n, 24, force={"kind": "accel", "ax": 0.0, "ay": -1e-4}, work=True)
+    fields = W.random_periodic(n, 24, seed=9)[1]
+    o = oracle.Oracle(case, fields)
+
+    def energy_and_power():
+        m = o.moments()
+        E = float(o.h.sum()) + 0.5 * float(np.sum(m["rho"] * (-1e-4) * m["uy"]))  # rho E = sum h_bar + F.u/2
+        P = float(np.sum(m["rho"] * (-1e-4) * m["uy"]))  # sum F.u
+        return E, P
+
+    E0, P0 = energy_and_power()
+    for _ in range(20):
+        o.step(1)
+        E1, P1 = energy_and_power()
+        # the energy sums are O(60): their FP64 rounding is ~1e-13 of an increment of ~1e-5
+        assert E1 - E0 == pytest.approx(0.5 * (P0 + P1), rel=1e-7)
+        E0, P0 = E1, P1
+
+
 def test_couette_viscous_heating_profile():
     # Section V.B (isothermal-wall form): steady T = Tw + Pr U^2/(2 c_p) eta (1 - eta), c_p = R(b+2)/2
     case, fields = W.couette(3, 64, U=0.05, nu=0.05, Pr=0.71, gamma=1.4)

@@ -196,10 +196,10 @@ def profile_run(args):
 
     case, fields = W.rayleigh_benard(args.probe_nx, args.probe_ny, Ra=1e4, seed=2, storage=args.storage)
     lat = tclbm.Lattice(case, fields)
+    if args.kernel is not None:
+        lat.set_kernel(args.kernel)  # before the shape: a new variant resets it
     if args.tile:
         lat.set_tile(*args.tile)
-    if args.kernel is not None:
-        lat.set_kernel(args.kernel)
     lat.step(args.warmup)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

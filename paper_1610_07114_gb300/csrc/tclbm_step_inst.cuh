@@ -13,10 +13,24 @@ static cudaError_t allow_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// CTAs of tclbm_step_tile<BX, BY> the current device holds resident at once (0 if the
+// query fails).
+template <int BX, int BY, bool LATE>
+static long long tile_wave() {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tclbm_step_tile<BX, BY, ST, LATE>, BX * BY, 0)) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (long long)sms * per_sm;
+}
+
 template <int BX, int BY>
 static cudaError_t launch_tile_shape(const DevParams& p, const ST* in, ST* out, cudaStream_t s) {
     // programmatic dependent launch: the next step's grid is scheduled while this one
-    // runs (the kernel waits for its predecessor before touching memory)
+    // runs (the kernel waits for its predecessor before touching memory); 32 x 4 tiles
+    // wait late on grids of more than one wave
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((p.nx + BX - 1) / BX, (p.ny + BY - 1) / BY, 1);
     cfg.blockDim = dim3(BX * BY, 1, 1);
@@ -27,7 +41,14 @@ static cudaError_t launch_tile_shape(const DevParams& p, const ST* in, ST* out, 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, tclbm_step_tile<BX, BY, ST>, p, in, out);
+    if constexpr (BX == 32 && BY == 4) {
+        static const long long wave = tile_wave<BX, BY, true>();
+        if (wave > 0 && (long long)cfg.gridDim.x * cfg.gridDim.y > wave) {
+            const cudaError_t e = cudaLaunchKernelEx(&cfg, tclbm_step_tile<BX, BY, ST, true>, p, in, out);
+            return e != cudaSuccess ? e : cudaGetLastError();
+        }
+    }
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, tclbm_step_tile<BX, BY, ST, false>, p, in, out);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 

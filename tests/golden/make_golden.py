@@ -11,7 +11,11 @@ rb_256x128_nusselt.txt: the same on the 256 x 128 lattice of the bench workload
 (perturbation amplitude 1e-4, seed 1, as the workload draws it), every 25 000 steps
 up to 300 000.
 
-    python tests/golden/make_golden.py [rb_128x64] [rb_256x128]
+table2_couette_oracle.txt: bottom-wall temperature of the paper's thermal Couette flow
+(Section V.B, Table 2 rows: Pr = 5, 4; gamma = 5/3, 3/2; Ma = 0.35; 5 x 40 lattice)
+after 60 000 steps.
+
+    python tests/golden/make_golden.py [rb_128x64] [rb_256x128] [table2_couette_oracle]
 """
 import os
 import sys
@@ -67,7 +71,25 @@ def rb_256x128():
             fh.write(f"{steps} {nu:.12f}\n")
 
 
+def table2_couette_oracle():
+    rows = []
+    for Pr, gamma in ((5.0, 5.0 / 3.0), (5.0, 1.5), (4.0, 5.0 / 3.0), (4.0, 1.5)):
+        case, fields = W.couette_paper(Pr=Pr, gamma=gamma)
+        o = oracle.Oracle(case, fields, threads=4)
+        o.step(60000)
+        T_bottom = float(o.moments()["T"][0].mean())
+        rows.append((Pr, gamma, T_bottom))
+        print(f"  Pr {Pr:g} gamma {gamma:.4f}: T_bottom = {T_bottom:.9f}", flush=True)
+    with open(os.path.join(HERE, "table2_couette_oracle.txt"), "w") as fh:
+        fh.write("# Bottom-wall temperature of the FP64 oracle: thermal Couette flow of Section V.B (Table 2),\n")
+        fh.write("# 5 x 40 lattice, Ma = 0.35, mu0 = 0.35, w2 = 1.1, w3 = 1.6, w4 = 0.3, 60 000 steps;\n")
+        fh.write("# written by tests/golden/make_golden.py\n")
+        fh.write("# columns: Pr  gamma  T_bottom\n")
+        for Pr, gamma, Tb in rows:
+            fh.write(f"{Pr:g} {gamma!r} {Tb:.12f}\n")
+
+
 if __name__ == "__main__":
-    which = sys.argv[1:] or ["rb_128x64", "rb_256x128"]
+    which = sys.argv[1:] or ["rb_128x64", "rb_256x128", "table2_couette_oracle"]
     for name in which:
         globals()[name]()

@@ -3,10 +3,14 @@
 mu / mu0 = T / T0, the paper's unequal rates w2 = 1.1, w3 = 1.6, w4 = 0.3.
 
 The analytic bottom temperature is T/T0 = 1 + Pr (gamma - 1) Ma^2 / 2.  With the paper's
-rates the steady heating comes out 3.6 % low, for every row, independent of Ma and of
-the mesh (the FP64 oracle gives the same; with w2 = w1 the heating is exact, an oracle
-pin), so the bound here is 4 % of the heating against the analytic and against the
-paper's numerical column (the paper reports 0.43-0.59 %).
+rates the scheme as read gives a steady heating 3.2-3.4 % low in every row; the FP64
+oracle gives the same, and the deficit does not converge away with the mesh (heating
+ratio 0.932 / 0.967 / 0.965 at ny = 20 / 40 / 80, Pr = 5).  It depends on the bulk rate
+w2, which cannot enter a divergence-free flow in the continuum limit (0.967 at w2 = 1.1,
+0.536 at 1.3): mostly through the wet moving-wall node's relaxation of E, the rest in the
+interior.  The GPU heating is pinned to the oracle's within 0.5 % of the heating
+(golden/table2_couette_oracle.txt, written from the oracle alone), and to the analytic
+value and the paper's numerical column within 4 % (the paper reports 0.43-0.59 %).
 """
 import os
 
@@ -34,6 +38,7 @@ def T():
 
 
 ROWS = np.loadtxt(os.path.join(HERE, "golden", "table2_couette.txt"))
+ORACLE = {(r[0], round(r[1], 6)): r[2] for r in np.loadtxt(os.path.join(HERE, "golden", "table2_couette_oracle.txt"))}
 
 
 @pytest.mark.parametrize("Pr,gamma,Tn_paper,Ta_paper", [tuple(r[:4]) for r in ROWS],
@@ -50,5 +55,8 @@ def test_bottom_wall_heating_matches_table2(T, Pr, gamma, Tn_paper, Ta_paper):
     ratio = (T_bottom - 1) / (Ta - 1)
     print(f"Pr {Pr:g} gamma {gamma:.3f}: T_bottom {T_bottom:.4f}, analytic {Ta:.4f}, paper {Tn_paper:.4f}, "
           f"heating ratio {ratio:.4f}")
+    T_oracle = ORACLE[(Pr, round(gamma, 6))]
+    print(f"  oracle T_bottom {T_oracle:.6f}, heating against the oracle's {(T_bottom - 1) / (T_oracle - 1):.5f}")
+    assert abs((T_bottom - 1) / (T_oracle - 1) - 1) < 0.005
     assert abs(ratio - 1) < 0.04
     assert abs((T_bottom - 1) / (Tn_paper - 1) - 1) < 0.04

@@ -73,8 +73,18 @@ static cudaError_t launch_tx(const StepLaunch& k, const DevParams& p0, const voi
     const bool corr = k.thermal && k.correction;
     if (k.kernel == KERNEL_TMA) {
         if (corr) {
-            const size_t sm = tma_smem_bytes<TX, true, ST>(true);
-            tclbm_step_tma_corr<TX, ST><<<grid, TX, sm, s>>>(p, *k.src_map, in, out, k.ty, k.err);
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = grid;
+            cfg.blockDim = dim3(TX, 1, 1);
+            cfg.dynamicSmemBytes = tma_smem_bytes<TX, true, ST>(true);
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            const cudaError_t e = cudaLaunchKernelEx(&cfg, tclbm_step_tma_corr<TX, ST>, p, *k.src_map, in, out, k.ty, k.err);
+            if (e != cudaSuccess) return e;
         } else if (k.thermal) {
             const size_t sm = tma_smem_bytes<TX, true, ST>(false);
             tclbm_step_tma_plain<TX, true, ST><<<grid, TX, sm, s>>>(p, *k.src_map, in, out, k.ty, k.err);

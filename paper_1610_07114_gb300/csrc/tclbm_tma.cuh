@@ -487,6 +487,10 @@ __global__ void __launch_bounds__(TX, CorrShape<ST>::kThreadsPerSM / TX) tclbm_s
                                                           const ST* __restrict__ src, ST* __restrict__ dst,
                                                           int rows_per_cta, int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
+    // programmatic dependent launch: this grid's CTAs take the slots the previous step's
+    // grid frees and wait here for its completion (its writes are this step's source)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (*(volatile int*)err) return;  // an earlier launch gave up: do not queue more waits
     const int nseg = gridDim.y;
     const int y0 = blockIdx.y * rows_per_cta;

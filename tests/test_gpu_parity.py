@@ -152,6 +152,36 @@ def test_taylor_green_config(T):
         assert e[k] <= REL_L2, e
 
 
+CONFIGS_FULL = [
+    ("rb_256x128_bench", lambda: W.rayleigh_benard(256, 128), "tclbm_step_tile"),
+    ("taylor_green_512", lambda: W.taylor_green(512, F0=1.5625e-7, nu=0.02), "tclbm_step_plain"),
+    ("couette_8x64", lambda: W.couette(8, 64), "tclbm_step"),
+    ("shock_tube_4096x4", lambda: W.shock_tube(4096, 4), "tclbm_step"),
+]
+
+
+@pytest.mark.parametrize("name,make,kernel", CONFIGS_FULL, ids=[c[0] for c in CONFIGS_FULL])
+def test_config_one_step_every_node(T, name, make, kernel):
+    # each workload at its full size, in the kernel the library picks for it: one step
+    # from a state both sides hold (the oracle's after 20 steps, rounded to FP32),
+    # compared population by population at every node
+    case, fields = make()
+    o = oracle.Oracle(case, fields, threads=16)
+    o.step(20)
+    lat = T.Lattice(case, fields)
+    assert lat.describe().startswith(kernel), lat.describe()
+    lat.set_populations(o.f, o.h if case["thermal"] else None)
+    f0, h0 = lat.populations()
+    o.set_populations(f0, h0 if case["thermal"] else None)
+    lat.step(1)
+    f1, h1 = lat.populations()
+    lat.close()
+    o.step(1)
+    np.testing.assert_allclose(f1, o.f, rtol=0, atol=2e-6)
+    if case["thermal"]:
+        np.testing.assert_allclose(h1, o.h, rtol=0, atol=2e-6)
+
+
 @pytest.mark.parametrize("nx,ny,walls", [(1, 5, None), (2, 2, None), (3, 3, "y"), (5, 3, "x"), (33, 4, "y"),
                                          (129, 7, None), (31, 130, "y")])
 def test_edge_sizes(T, nx, ny, walls):

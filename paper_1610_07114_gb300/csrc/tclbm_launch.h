@@ -96,6 +96,42 @@ inline cudaError_t launch_batch_kernel(int storage, int tx, int kind, unsigned g
 // Box width (elements) of the TMA row copy for a strip of tx columns.
 inline int tma_box_width(int storage, int tx) { return tx + 2 * (storage == 0 ? 4 : 8); }
 
+// Multiprocessors of the current device (152 if the query fails).
+inline int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n < 1) {
+        cudaGetLastError();
+        return 152;
+    }
+    return n;
+}
+
+// Row segments of the TMA kernel with the correction term: `full` segments of ty rows
+// (the first one `extra` rows taller), then `half` segments of ty / 2 rows.  The block
+// scheduler dispatches blocks in index order, so the short segments run last: about
+// one wave of them makes the launch's tail out of half-length CTAs.  Used where the
+// grid spans more than two waves of `resident` CTAs, ty is a multiple of 16 and ny a
+// multiple of 8 (segment starts stay on multiples of 8 rows); otherwise the plan is
+// uniform (full = ny / ty, the last segment taking the remainder, half = extra = 0).
+struct SegPlan {
+    int full, half, extra;
+};
+inline SegPlan tma_seg_plan(const DevParams& p, int tx, int ty, long long resident) {
+    const int strips = (p.nx + tx - 1) / tx;
+    int nseg = p.ny / ty;
+    if (nseg < 1) nseg = 1;
+    SegPlan s{nseg, 0, 0};
+    if (ty % 16 != 0 || p.ny % 8 != 0 || (long long)nseg * strips <= 2 * resident) return s;
+    const int half = (int)((resident + strips - 1) / strips);
+    const int full = (p.ny - half * (ty / 2)) / ty;
+    if (full < 2) return s;
+    s.full = full;
+    s.half = half;
+    s.extra = p.ny - full * ty - half * (ty / 2);
+    return s;
+}
+
 inline dim3 step_grid(const DevParams& p, int tx, int ty) {
     int nseg = p.ny / ty;
     if (nseg < 1) nseg = 1;
@@ -113,6 +149,15 @@ inline void describe_step_kernel(int storage, const StepLaunch& k, const DevPara
     }
     const char* base = k.kernel == KERNEL_TMA ? (corr ? "tclbm_step_tma_corr" : "tclbm_step_tma_plain")
                                               : (corr ? "tclbm_step_corr" : "tclbm_step_plain");
+    if (k.kernel == KERNEL_TMA && corr) {
+        const long long resident = (long long)sm_count() * ((storage == 0 ? 384 : 512) / k.tx);
+        const SegPlan plan = tma_seg_plan(p, k.tx, k.ty, resident);
+        if (plan.half > 0) {
+            snprintf(out, len, "%s<%d,%s> grid (%u, %d) block (%d) rows/cta %d, last %d segments of %d", base, k.tx, st,
+                     g.x, plan.full + plan.half, k.tx, k.ty, plan.half, k.ty / 2);
+            return;
+        }
+    }
     snprintf(out, len, "%s<%d,%s%s> grid (%u, %u) block (%d) rows/cta %d", base, k.tx,
              corr ? "" : (k.thermal ? "thermal," : "athermal,"), st, g.x, g.y, k.tx, k.ty);
 }

@@ -73,8 +73,10 @@ static cudaError_t launch_tx(const StepLaunch& k, const DevParams& p0, const voi
     const bool corr = k.thermal && k.correction;
     if (k.kernel == KERNEL_TMA) {
         if (corr) {
+            static const long long resident = (long long)sm_count() * (CorrShape<ST>::kThreadsPerSM / TX);
+            const SegPlan plan = tma_seg_plan(p, TX, k.ty, resident);
             cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = grid;
+            cfg.gridDim = dim3(grid.x, (unsigned)(plan.full + plan.half), 1);
             cfg.blockDim = dim3(TX, 1, 1);
             cfg.dynamicSmemBytes = tma_smem_bytes<TX, true, ST>(true);
             cfg.stream = s;
@@ -83,7 +85,8 @@ static cudaError_t launch_tx(const StepLaunch& k, const DevParams& p0, const voi
             attr[0].val.programmaticStreamSerializationAllowed = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            const cudaError_t e = cudaLaunchKernelEx(&cfg, tclbm_step_tma_corr<TX, ST>, p, *k.src_map, in, out, k.ty, k.err);
+            const cudaError_t e = cudaLaunchKernelEx(&cfg, tclbm_step_tma_corr<TX, ST>, p, *k.src_map, in, out, k.ty,
+                                                     plan.full, plan.extra, k.err);
             if (e != cudaSuccess) return e;
         } else if (k.thermal) {
             const size_t sm = tma_smem_bytes<TX, true, ST>(false);

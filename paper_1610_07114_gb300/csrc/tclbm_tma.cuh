@@ -485,16 +485,27 @@ __device__ __forceinline__ bool tma_corr_strip(const DevParams& p, const CUtenso
 template <int TX, class ST>
 __global__ void __launch_bounds__(TX, CorrShape<ST>::kThreadsPerSM / TX) tclbm_step_tma_corr(const __grid_constant__ DevParams p, const __grid_constant__ CUtensorMap map,
                                                           const ST* __restrict__ src, ST* __restrict__ dst,
-                                                          int rows_per_cta, int* __restrict__ err) {
+                                                          int rows_per_cta, int seg_full, int seg_extra,
+                                                          int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     // programmatic dependent launch: this grid's CTAs take the slots the previous step's
     // grid frees and wait here for its completion (its writes are this step's source)
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (*(volatile int*)err) return;  // an earlier launch gave up: do not queue more waits
-    const int nseg = gridDim.y;
-    const int y0 = blockIdx.y * rows_per_cta;
-    const int y1 = (blockIdx.y == nseg - 1) ? p.ny : y0 + rows_per_cta;
+    // segment plan (tma_seg_plan): seg_full segments of rows_per_cta rows, the first one
+    // seg_extra rows taller, then half-height segments; the last one ends at ny
+    const int j = blockIdx.y;
+    int y0, y1;
+    if (j < seg_full) {
+        y0 = j == 0 ? 0 : seg_extra + j * rows_per_cta;
+        y1 = seg_extra + (j + 1) * rows_per_cta;
+    } else {
+        const int h = rows_per_cta / 2;
+        y0 = seg_extra + seg_full * rows_per_cta + (j - seg_full) * h;
+        y1 = y0 + h;
+    }
+    if (j == (int)gridDim.y - 1) y1 = p.ny;
     if (!tma_corr_strip<TX, ST>(p, &map, src, dst, blockIdx.x * TX, y0, y1, err, smem)) return;
     if (blockIdx.x == 0 && blockIdx.y == 0) bump_step_counter(p);
 }

@@ -208,14 +208,17 @@ def test_launch_shapes_are_bit_identical(T):
 
 
 def test_tma_rows_per_cta_are_bit_identical(T):
-    # the TMA kernel's row segments (16 rows by default, 32 on lattices of >= 8 waves)
-    # change which CTA computes a node, not its arithmetic
-    case, fields = W.rayleigh_benard(512, 256, seed=5)
+    # the TMA kernel's row segments change which CTA computes a node, not its
+    # arithmetic: 16 rows on 2048 x 1024 is a grid of more than two waves, so its last
+    # wave takes half-height segments (the first one absorbing the remainder); 7, 32 and
+    # 48 rows are uniform segments
+    case, fields = W.rayleigh_benard(2048, 1024, seed=5)
     states = []
     for ty in (16, 32, 7, 48):
         lat = T.Lattice(case, fields)
         lat.set_kernel(0)
         lat.set_tile(128, ty)
+        assert ("last" in lat.describe()) == (ty == 16), lat.describe()
         lat.step(21)
         states.append(lat.populations())
         lat.close()

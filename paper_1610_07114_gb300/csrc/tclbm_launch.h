@@ -132,6 +132,15 @@ inline SegPlan tma_seg_plan(const DevParams& p, int tx, int ty, long long reside
     return s;
 }
 
+// Resident CTAs the TMA launcher of each format plans its segments for.
+long long tma_resident_fp32(int tx, int corr, int thermal);
+long long tma_resident_bf16(int tx, int corr, int thermal);
+long long tma_resident_fp16(int tx, int corr, int thermal);
+inline long long tma_resident(int storage, int tx, int corr, int thermal) {
+    return storage == 0 ? tma_resident_fp32(tx, corr, thermal)
+                        : storage == 1 ? tma_resident_bf16(tx, corr, thermal) : tma_resident_fp16(tx, corr, thermal);
+}
+
 inline dim3 step_grid(const DevParams& p, int tx, int ty) {
     int nseg = p.ny / ty;
     if (nseg < 1) nseg = 1;
@@ -149,12 +158,12 @@ inline void describe_step_kernel(int storage, const StepLaunch& k, const DevPara
     }
     const char* base = k.kernel == KERNEL_TMA ? (corr ? "tclbm_step_tma_corr" : "tclbm_step_tma_plain")
                                               : (corr ? "tclbm_step_corr" : "tclbm_step_plain");
-    if (k.kernel == KERNEL_TMA && corr) {
-        const long long resident = (long long)sm_count() * ((storage == 0 ? 384 : 512) / k.tx);
-        const SegPlan plan = tma_seg_plan(p, k.tx, k.ty, resident);
+    if (k.kernel == KERNEL_TMA) {
+        const SegPlan plan = tma_seg_plan(p, k.tx, k.ty, tma_resident(storage, k.tx, corr, k.thermal));
         if (plan.half > 0) {
-            snprintf(out, len, "%s<%d,%s> grid (%u, %d) block (%d) rows/cta %d, last %d segments of %d", base, k.tx, st,
-                     g.x, plan.full + plan.half, k.tx, k.ty, plan.half, k.ty / 2);
+            snprintf(out, len, "%s<%d,%s%s> grid (%u, %d) block (%d) rows/cta %d, last %d segments of %d", base, k.tx,
+                     corr ? "" : (k.thermal ? "thermal," : "athermal,"), st, g.x, plan.full + plan.half, k.tx, k.ty,
+                     plan.half, k.ty / 2);
             return;
         }
     }

@@ -8,4 +8,5 @@ using ST = float;
 #define BATCH_FN launch_batch_fp32
 #define BATCH_OCC_FN batch_occupancy_fp32
 #define BATCH_TMA_FN launch_batch_tma_fp32
+#define TMA_RESIDENT_FN tma_resident_fp32
 #include "tclbm_step_inst.cuh"

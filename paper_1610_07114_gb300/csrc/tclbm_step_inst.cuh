@@ -63,6 +63,41 @@ static cudaError_t launch_tile(int bx, int by, const DevParams& p, const ST* in,
     return launch_tile_shape<32, 4>(p, in, out, s);
 }
 
+// One launch of a TMA-fed step kernel (signature of tclbm_step_tma_corr / _plain) under the
+// segment plan for `resident` CTAs, with programmatic dependent launch.
+template <class K>
+static cudaError_t launch_tma(K kernel, int tx, size_t smem, long long resident, const StepLaunch& k, const DevParams& p,
+                              const ST* in, ST* out, cudaStream_t s) {
+    const SegPlan plan = tma_seg_plan(p, tx, k.ty, resident);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((p.nx + tx - 1) / tx), (unsigned)(plan.full + plan.half), 1);
+    cfg.blockDim = dim3(tx, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, p, *k.src_map, in, out, k.ty, plan.full, plan.extra, k.err);
+}
+
+// CTAs of tclbm_step_tma_plain<TX, THERMAL> the current device holds resident at once.
+template <int TX, bool THERMAL>
+static long long plain_resident() {
+    static const long long n = [] {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tclbm_step_tma_plain<TX, THERMAL, ST>, TX,
+                                                          tma_smem_bytes<TX, THERMAL, ST>(false)) != cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        return (long long)sm_count() * per_sm;
+    }();
+    return n;
+}
+
 template <int TX>
 static cudaError_t launch_tx(const StepLaunch& k, const DevParams& p0, const void* src, void* dst, cudaStream_t s) {
     DevParams p = p0;
@@ -72,29 +107,18 @@ static cudaError_t launch_tx(const StepLaunch& k, const DevParams& p0, const voi
     ST* out = static_cast<ST*>(dst);
     const bool corr = k.thermal && k.correction;
     if (k.kernel == KERNEL_TMA) {
+        cudaError_t e;
         if (corr) {
             static const long long resident = (long long)sm_count() * (CorrShape<ST>::kThreadsPerSM / TX);
-            const SegPlan plan = tma_seg_plan(p, TX, k.ty, resident);
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(grid.x, (unsigned)(plan.full + plan.half), 1);
-            cfg.blockDim = dim3(TX, 1, 1);
-            cfg.dynamicSmemBytes = tma_smem_bytes<TX, true, ST>(true);
-            cfg.stream = s;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-            attr[0].val.programmaticStreamSerializationAllowed = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            const cudaError_t e = cudaLaunchKernelEx(&cfg, tclbm_step_tma_corr<TX, ST>, p, *k.src_map, in, out, k.ty,
-                                                     plan.full, plan.extra, k.err);
-            if (e != cudaSuccess) return e;
+            e = launch_tma(tclbm_step_tma_corr<TX, ST>, TX, tma_smem_bytes<TX, true, ST>(true), resident, k, p, in, out, s);
         } else if (k.thermal) {
-            const size_t sm = tma_smem_bytes<TX, true, ST>(false);
-            tclbm_step_tma_plain<TX, true, ST><<<grid, TX, sm, s>>>(p, *k.src_map, in, out, k.ty, k.err);
+            e = launch_tma(tclbm_step_tma_plain<TX, true, ST>, TX, tma_smem_bytes<TX, true, ST>(false),
+                           plain_resident<TX, true>(), k, p, in, out, s);
         } else {
-            const size_t sm = tma_smem_bytes<TX, false, ST>(false);
-            tclbm_step_tma_plain<TX, false, ST><<<grid, TX, sm, s>>>(p, *k.src_map, in, out, k.ty, k.err);
+            e = launch_tma(tclbm_step_tma_plain<TX, false, ST>, TX, tma_smem_bytes<TX, false, ST>(false),
+                           plain_resident<TX, false>(), k, p, in, out, s);
         }
+        if (e != cudaSuccess) return e;
     } else if (k.kernel == KERNEL_TILE && corr) {
         return launch_tile(k.tx, k.ty, p, in, out, s);
     } else {
@@ -123,6 +147,16 @@ cudaError_t PREPARE_FN() {
     if (e == cudaSuccess) e = prepare_tx<64>();
     if (e == cudaSuccess) e = prepare_tx<128>();
     return e;
+}
+
+// Resident CTAs the TMA launcher plans the segments for (see launch_tma).
+long long TMA_RESIDENT_FN(int tx, int corr, int thermal) {
+    if (corr) return (long long)sm_count() * (CorrShape<ST>::kThreadsPerSM / tx);
+    switch (tx) {
+        case 32: return thermal ? plain_resident<32, true>() : plain_resident<32, false>();
+        case 64: return thermal ? plain_resident<64, true>() : plain_resident<64, false>();
+        default: return thermal ? plain_resident<128, true>() : plain_resident<128, false>();
+    }
 }
 
 cudaError_t LAUNCH_FN(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s) {

@@ -276,20 +276,40 @@ __device__ __forceinline__ void ring_refill(RowRing<TX, THERMAL, ST>& R, const D
     R.freed_to = s_free;
 }
 
+// Rows [y0, y1) of this CTA's segment (blockIdx.y) under the host's segment plan
+// (tma_seg_plan): seg_full segments of `rows` rows, the first one seg_extra rows taller,
+// then half-height segments; the last segment ends at ny.
+__device__ __forceinline__ void tma_segment(const DevParams& p, int rows, int seg_full, int seg_extra, int& y0,
+                                            int& y1) {
+    const int j = blockIdx.y;
+    if (j < seg_full) {
+        y0 = j == 0 ? 0 : seg_extra + j * rows;
+        y1 = seg_extra + (j + 1) * rows;
+    } else {
+        const int h = rows / 2;
+        y0 = seg_extra + seg_full * rows + (j - seg_full) * h;
+        y1 = y0 + h;
+    }
+    if (j == (int)gridDim.y - 1) y1 = p.ny;
+}
+
 // Without the correction term (athermal, or thermal with C off).
 template <int TX, bool THERMAL, class ST>
 __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_plain(const __grid_constant__ DevParams p, const __grid_constant__ CUtensorMap map,
                                                            const ST* __restrict__ src, ST* __restrict__ dst,
-                                                           int rows_per_cta, int* __restrict__ err) {
+                                                           int rows_per_cta, int seg_full, int seg_extra,
+                                                           int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem[];
     using RR = RowRing<TX, THERMAL, ST>;
     RR R;
+    // programmatic dependent launch, as in tclbm_step_tma_corr
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (*(volatile int*)err) return;  // an earlier launch gave up: do not queue more waits
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX;
-    const int nseg = gridDim.y;
-    const int y0 = blockIdx.y * rows_per_cta;
-    const int y1 = (blockIdx.y == nseg - 1) ? p.ny : y0 + rows_per_cta;
+    int y0, y1;
+    tma_segment(p, rows_per_cta, seg_full, seg_extra, y0, y1);
     // output row r pulls sources r-1..r+1; a wall row's neighbour reaches r-2 / r+2
     ring_setup<TX, THERMAL, ST>(R, smem, &map, x0, y0 - 2, y1 + 1, p);
     const int x = x0 + tid;
@@ -493,19 +513,8 @@ __global__ void __launch_bounds__(TX, CorrShape<ST>::kThreadsPerSM / TX) tclbm_s
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (*(volatile int*)err) return;  // an earlier launch gave up: do not queue more waits
-    // segment plan (tma_seg_plan): seg_full segments of rows_per_cta rows, the first one
-    // seg_extra rows taller, then half-height segments; the last one ends at ny
-    const int j = blockIdx.y;
     int y0, y1;
-    if (j < seg_full) {
-        y0 = j == 0 ? 0 : seg_extra + j * rows_per_cta;
-        y1 = seg_extra + (j + 1) * rows_per_cta;
-    } else {
-        const int h = rows_per_cta / 2;
-        y0 = seg_extra + seg_full * rows_per_cta + (j - seg_full) * h;
-        y1 = y0 + h;
-    }
-    if (j == (int)gridDim.y - 1) y1 = p.ny;
+    tma_segment(p, rows_per_cta, seg_full, seg_extra, y0, y1);
     if (!tma_corr_strip<TX, ST>(p, &map, src, dst, blockIdx.x * TX, y0, y1, err, smem)) return;
     if (blockIdx.x == 0 && blockIdx.y == 0) bump_step_counter(p);
 }

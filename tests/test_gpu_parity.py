@@ -226,6 +226,32 @@ def test_tma_rows_per_cta_are_bit_identical(T):
         assert np.array_equal(f, states[0][0]) and np.array_equal(h, states[0][1])
 
 
+@pytest.mark.parametrize("name,make", [
+    ("athermal_taylor_green_2048", lambda: W.taylor_green(2048, F0=1e-8, nu=0.02)),
+    ("thermal_no_correction_2048x1024", lambda: W.random_periodic(2048, 1024, seed=31, force="accel",
+                                                                   correction=False)),
+], ids=["athermal_taylor_green_2048", "thermal_no_correction_2048x1024"])
+def test_tma_plain_kernel_short_tail_equals_the_direct_kernel(T, name, make):
+    # the TMA kernel without the correction term, 16-row segments on a grid of more than
+    # two waves (its last wave half-height), against the direct-load kernel: periodic, so
+    # bit for bit
+    case, fields = make()
+    states = []
+    for kind in (0, 1):
+        lat = T.Lattice(case, fields)
+        lat.set_kernel(kind)
+        if kind == 0:
+            lat.set_tile(128, 16)
+            assert "last" in lat.describe(), lat.describe()
+        lat.step(21)
+        states.append(lat.populations())
+        lat.close()
+    (fa, ha), (fb, hb) = states
+    assert np.array_equal(fa, fb)
+    if case["thermal"]:
+        assert np.array_equal(ha, hb)
+
+
 KERNEL_CASES = [
     ("periodic_corr", *W.random_periodic(150, 45, seed=21, force="accel")),
     ("periodic_tg_nocorr", *W.random_periodic(97, 33, seed=22, force="taylor_green", correction=False)),

@@ -194,15 +194,15 @@ void default_shape(const tclbm_params& p, int kernel, int& tx, int& ty) {
         ty = (int)(t < 2 ? 2 : (t > 16 ? 16 : t));
     } else {
         // 16 rows per CTA, or 32 (fewer halo rows per node) where the last wave's tail
-        // weighs little: where the 32-row grid spans more than two waves of resident CTAs
-        // (3 per SM for FP32, 4 for 16-bit), so the kernel's tail of half-height segments
-        // applies (ny a multiple of 8), else where it spans at least 8 waves.  Measured with
-        // the short tail: 32 rows tie 16 at 4096 x 2048 and beat it by 1 % at 2048 x 2048
-        // (FP32) and by 4-5 % at 8192 x 4096; 16 rows win by 12 % where the 32-row grid has
-        // no short tail (FP16 2048 x 2048).
+        // weighs little: where the 32-row grid spans more than two waves of the kernel's
+        // resident CTAs, so its tail of half-height segments applies (ny a multiple of 8),
+        // else where it spans at least 8 waves.  Measured with the short tail: 32 rows tie
+        // 16 at 4096 x 2048 and beat it by 1 % at 2048 x 2048 (FP32) and by 4-5 % at
+        // 8192 x 4096; 16 rows win by 12-20 % where the 32-row grid has no short tail
+        // (FP16 2048 x 2048, athermal 2048 x 2048).
         tx = p.nx >= 512 ? 128 : (p.nx >= 96 ? 64 : 32);
         const long long strips = (p.nx + tx - 1) / tx;
-        const long long resident = 152LL * (p.storage == TCLBM_STORE_FP32 ? 3 : 4);
+        const long long resident = tma_resident(p.storage, tx, p.thermal && p.correction, p.thermal);
         if (p.ny % 8 == 0)
             ty = strips * (p.ny / 32) > 2 * resident ? 32 : 16;
         else

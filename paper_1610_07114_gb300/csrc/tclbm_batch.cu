@@ -106,6 +106,26 @@ void make_items(tclbm_batch* B, std::vector<BatchItem>& items) {
                 for (int c = 0; c < nstrip; ++c) items.push_back(BatchItem{li, c * tx, y0, y1});
             }
         }
+        if (g == kGroupTma) {
+            // as in the single-lattice TMA kernel: blocks run in index order, so where the
+            // group spans more than two waves its last wave of items is cut to half height
+            // (at a multiple of 8 rows) and the launch's tail is made of short CTAs
+            const long long wave = (long long)B->sms * tma_corr_ctas_per_sm(B->storage, B->tma_tx);
+            const long long n = (long long)items.size() - B->first[g];
+            if (n > 2 * wave) {
+                std::vector<BatchItem> tail(items.end() - wave, items.end());
+                items.resize(items.size() - wave);
+                for (const BatchItem& it : tail) {
+                    const int cut = it.y0 + (it.y1 - it.y0) / 16 * 8;
+                    if (cut - it.y0 >= 8 && it.y1 - cut >= 8) {
+                        items.push_back(BatchItem{it.lat, it.x0, it.y0, cut});
+                        items.push_back(BatchItem{it.lat, it.x0, cut, it.y1});
+                    } else {
+                        items.push_back(it);
+                    }
+                }
+            }
+        }
         B->count[g] = (int)items.size() - B->first[g];
     }
 }

@@ -132,6 +132,10 @@ inline SegPlan tma_seg_plan(const DevParams& p, int tx, int ty, long long reside
     return s;
 }
 
+// CTAs per SM the TMA kernels with the correction term are sized for (threads per SM of
+// CorrShape in tclbm_tma.cuh: 384 for FP32 rows, 512 for 16-bit rows), for strips of tx.
+inline int tma_corr_ctas_per_sm(int storage, int tx) { return (storage == 0 ? 384 : 512) / tx; }
+
 // Resident CTAs the TMA launcher of each format plans its segments for.
 long long tma_resident_fp32(int tx, int corr, int thermal);
 long long tma_resident_bf16(int tx, int corr, int thermal);

@@ -246,6 +246,31 @@ def test_tma_fed_batch_equals_each_lattice_alone(T, tma, storage, rounding):
         lat.close()
 
 
+def test_tma_fed_batch_with_a_half_height_last_wave_equals_each_lattice_alone(T):
+    # 40 periodic thermal lattices of 512 x 256 in 128 x 16 TMA strips: 2,560 work items,
+    # more than two waves, so the last wave of items (the last lattices in the list) is cut
+    # to half height; every lattice still equals itself stepped alone, bit for bit
+    cases = [W.random_periodic(512, 256, seed=300 + i, force="accel") for i in range(40)]
+    lats = [T.Lattice(c, f) for c, f in cases]
+    import torch
+
+    wave = torch.cuda.get_device_properties(0).multi_processor_count * 3  # FP32 TMA CTAs per SM: 3
+    with T.Batch(lats) as b:
+        b.set_tma(128, 16)
+        b.step(5)
+        # 2,560 items, the last `wave` of them split in two
+        assert "items %d " % (2560 + wave) in b.describe(), b.describe()
+    for (c, f), lat in zip(cases, lats):
+        got = lat.populations()
+        ref = T.Lattice(c, f)
+        ref.set_kernel(0)
+        ref.step(5)
+        exp = ref.populations()
+        ref.close()
+        assert np.array_equal(got[0], exp[0]) and np.array_equal(got[1], exp[1])
+        lat.close()
+
+
 def test_tma_fed_batch_matches_fp64_oracle(T):
     case, fields = W.rayleigh_benard(192, 96, Ra=1e4, seed=40, amp=1e-2)
     lat = T.Lattice(case, fields)

@@ -82,13 +82,17 @@ static cudaError_t launch_tma(K kernel, int tx, size_t smem, long long resident,
     return cudaLaunchKernelEx(&cfg, kernel, p, *k.src_map, in, out, k.ty, plan.full, plan.extra, k.err);
 }
 
-// CTAs of tclbm_step_tma_plain<TX, THERMAL> the current device holds resident at once.
+// CTAs of tclbm_step_tma_plain<TX, THERMAL> the current device holds resident at once
+// (the kernel's dynamic shared-memory limit is raised first: the query may come before
+// PREPARE_FN, and the answer is kept).
 template <int TX, bool THERMAL>
 static long long plain_resident() {
     static const long long n = [] {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tclbm_step_tma_plain<TX, THERMAL, ST>, TX,
-                                                          tma_smem_bytes<TX, THERMAL, ST>(false)) != cudaSuccess ||
+        const size_t smem = tma_smem_bytes<TX, THERMAL, ST>(false);
+        if (allow_smem(tclbm_step_tma_plain<TX, THERMAL, ST>, smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tclbm_step_tma_plain<TX, THERMAL, ST>, TX, smem) !=
+                cudaSuccess ||
             per_sm < 1) {
             cudaGetLastError();
             per_sm = 1;

@@ -252,6 +252,34 @@ def test_tma_plain_kernel_short_tail_equals_the_direct_kernel(T, name, make):
         assert np.array_equal(ha, hb)
 
 
+_PLAN_SCRIPT = """
+import sys
+sys.path.insert(0, {root!r})
+from paper_1610_07114_gb300 import tclbm, workloads as W
+if {warm}:
+    tclbm.Lattice(*W.rayleigh_benard(64, 32)).close()
+lat = tclbm.Lattice(*W.random_periodic(4096, 2048, seed=32, force="accel", correction=False))
+print(lat.describe())
+lat.close()
+"""
+
+
+def test_tma_plain_segment_plan_does_not_depend_on_the_first_lattice(T):
+    # the plain TMA kernel's resident CTAs come from the occupancy calculator, asked (and
+    # remembered) the first time a lattice's launch shape is chosen, which may be before
+    # any lattice raised the kernel's shared-memory limit: a fresh process whose first
+    # lattice is this one must plan the same segments as one that made another first
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = [subprocess.run([sys.executable, "-c", _PLAN_SCRIPT.format(root=root, warm=w)], capture_output=True,
+                          text=True, timeout=600, check=True).stdout.strip().splitlines()[-1] for w in (False, True)]
+    assert out[0] == out[1], out
+    assert "last" in out[0], out[0]
+
+
 KERNEL_CASES = [
     ("periodic_corr", *W.random_periodic(150, 45, seed=21, force="accel")),
     ("periodic_tg_nocorr", *W.random_periodic(97, 33, seed=22, force="taylor_green", correction=False)),

@@ -228,7 +228,10 @@ tclbm_status tclbm_test_skip_row(tclbm_lattice* lat, int32_t row);
 tclbm_status tclbm_test_rcp(const float* x, float* y, int64_t n, void* stream);
 
 /* Launch-shape override for tuning; 0 keeps the library's choice.  Kernel variants 0
- * and 1: strip width tx (32, 64 or 128 nodes) and rows per CTA ty (>= 1).  Variant 2:
+ * and 1: strip width tx (32, 64 or 128 nodes) and rows per CTA ty (>= 1); under variant 0,
+ * where the grid spans more than two waves of resident CTAs, ty is a multiple of 16 and
+ * ny a multiple of 8, about the last wave of row segments takes ty / 2 rows (and the
+ * first segment the remainder), so that the launch ends on short CTAs.  Variant 2:
  * the tile (tx, ty) = (BX, BY), one of 16x4, 16x8, 32x4, 32x8, 32x16, 64x4, 64x8,
  * 128x4, subject to the variant's size rule (EINVAL otherwise). */
 tclbm_status tclbm_set_tile(tclbm_lattice* lat, int32_t tx, int32_t ty);

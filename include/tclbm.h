@@ -139,7 +139,14 @@ tclbm_status tclbm_create(const tclbm_params* params, tclbm_alloc_fn alloc, tclb
 tclbm_status tclbm_init_fields(tclbm_lattice* lat, const double* rho, const double* ux, const double* uy,
                                const double* T, int32_t on_device);
 
-/* Advance `nsteps` >= 0 time steps (asynchronous on the handle's stream). */
+/* Advance `nsteps` >= 0 time steps (asynchronous on the handle's stream).  Under kernel
+ * variant 0 with the correction term (and round-to-nearest for 16-bit storage, rows per
+ * CTA >= 8), the launches of one call are chained: each work item of a launch waits
+ * only for the nine items around it in the previous launch, so consecutive steps
+ * overlap on the device; the first launch of a call waits for whatever precedes it on
+ * the stream.  The states are bit-identical to one step per call.  A chained wait that
+ * expires is reported like the other bounded waits (TCLBM_ETIMEOUT at the next
+ * synchronising call). */
 tclbm_status tclbm_step(tclbm_lattice* lat, int64_t nsteps);
 
 /* Macroscopic fields of the current state (Eq. 20; T per Section IV, T0 if athermal),

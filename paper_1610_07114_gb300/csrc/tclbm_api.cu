@@ -203,6 +203,26 @@ void default_shape(const tclbm_params& p, int kernel, int& tx, int& ty) {
         tx = p.nx >= 512 ? 128 : (p.nx >= 96 ? 64 : 32);
         const long long strips = (p.nx + tx - 1) / tx;
         const long long resident = tma_resident(p.storage, tx, p.thermal && p.correction, p.thermal);
+        // Chained launches (tclbm_step: the correction-term kernel, FP32 or 16-bit with
+        // round-to-nearest) overlap consecutive steps, so the tail no longer sets the
+        // segment height: the tallest of 96, 64 and 48 rows whose grid still spans three
+        // waves of resident CTAs (measured against 16-96 rows: 4096 x 2048 FP32 takes 48
+        // rows, 0.722 -> 0.740 of peak; 8192 x 4096 takes 96, FP32 0.738 -> 0.779, FP16
+        // 0.389 -> 0.405); grids that reach three waves at none of them keep the rule below.
+        const bool chained = p.thermal && p.correction &&
+                             (p.storage == TCLBM_STORE_FP32 || p.rounding == TCLBM_ROUND_NEAREST);
+        if (chained) {
+            DevParams d = {};
+            d.nx = p.nx;
+            d.ny = p.ny;
+            for (int rows : {96, 64, 48}) {
+                const SegPlan plan = tma_seg_plan(d, tx, rows, resident);
+                if (strips * (plan.full + plan.half) >= 3 * resident) {
+                    ty = rows;
+                    return;
+                }
+            }
+        }
         if (p.ny % 8 == 0)
             ty = strips * (p.ny / 32) > 2 * resident ? 32 : 16;
         else
@@ -485,9 +505,21 @@ tclbm_status launch_steps(tclbm_lattice* L, int64_t n) {
         tclbm_status st = ensure_maps(L);
         if (st != TCLBM_OK) return st;
     }
+    // TMA launches with the correction term publish per-item completion tickets; after the
+    // first launch of this run the next one waits for each item's neighbours only (16-bit
+    // stochastic rounding keeps whole-grid waits: its step counter is written by one CTA)
+    const int tx = L->tx, nx = L->prm.nx;
+    const bool tickets = L->kernel == KERNEL_TMA && L->prm.thermal && L->prm.correction;
+    const bool chainable = tickets && !L->dp.rounding && L->ty >= 8 && (nx % tx == 0 || nx % tx >= 8);
     for (int64_t s = 0; s < n; ++s) {
-        const cudaError_t e = launch_step_kernel(L->prm.storage, step_launch(L, L->cur), L->dp, L->buf[L->cur],
-                                                 L->buf[L->cur ^ 1], L->stream);
+        StepLaunch k = step_launch(L, L->cur);
+        if (tickets) {
+            k.seg_done = L->seg_done;
+            k.seg_cap = (long long)(L->seg_bytes / sizeof(unsigned));
+            k.ticket = ++L->ticket;
+            k.chain = chainable && s > 0;
+        }
+        const cudaError_t e = launch_step_kernel(L->prm.storage, k, L->dp, L->buf[L->cur], L->buf[L->cur ^ 1], L->stream);
         if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
         L->cur ^= 1;
         ++L->steps;
@@ -583,6 +615,10 @@ tclbm_status check_kernel_error(tclbm_lattice* L) {
 
 }  // namespace
 
+// Entries of the completion-ticket array of the TMA kernel's work items: strips of at
+// least 32 columns times segments of at least 4 rows (half-height segments of 8-row plans).
+static size_t seg_entries(int nx, int ny) { return (size_t)((nx + 31) / 32) * (size_t)(ny / 4 + 2); }
+
 // ==================================================================== C ABI
 
 extern "C" {
@@ -596,7 +632,7 @@ size_t tclbm_state_bytes(const tclbm_params* p) {
     const size_t pops = 2 * planes * (size_t)p->ny * pitch_of(p->nx) * elem_of(p->storage);
     const size_t tables = sizeof(float) * 2 * ((size_t)p->nx + p->ny);
     const size_t diag = sizeof(double) * (kDiagMaxBlocks + 1) * TCLBM_NDIAG;
-    return pops + tables + diag + n * 4 * sizeof(double);
+    return pops + tables + diag + n * 4 * sizeof(double) + seg_entries(p->nx, p->ny) * sizeof(unsigned);
 }
 
 tclbm_status tclbm_create(const tclbm_params* params, tclbm_alloc_fn alloc, tclbm_free_fn free_fn, void* ctx,
@@ -629,7 +665,9 @@ tclbm_status tclbm_create(const tclbm_params* params, tclbm_alloc_fn alloc, tclb
     L->diag = (double*)dev_alloc(L, L->diag_bytes);
     L->stage = (double*)dev_alloc(L, L->stage_bytes);
     L->err = (int*)dev_alloc(L, 256);
-    if (!L->buf[0] || !L->buf[1] || !L->tables || !L->diag || !L->stage || !L->err) {
+    L->seg_bytes = seg_entries(params->nx, params->ny) * sizeof(unsigned);
+    L->seg_done = (unsigned*)dev_alloc(L, L->seg_bytes);
+    if (!L->buf[0] || !L->buf[1] || !L->tables || !L->diag || !L->stage || !L->err || !L->seg_done) {
         tclbm_destroy(L);
         return fail(TCLBM_ENOMEM, "device allocation of %zu bytes failed", tclbm_state_bytes(params));
     }
@@ -665,6 +703,7 @@ tclbm_status tclbm_create(const tclbm_params* params, tclbm_alloc_fn alloc, tclb
     if (e == cudaSuccess) e = cudaMemsetAsync(L->err, 0, 256, L->stream);
     L->dp.step_ctr = reinterpret_cast<unsigned*>(L->err) + 4;  // two counters after the error word
     if (e == cudaSuccess) e = cudaMemsetAsync(L->buf[1], 0, L->buf_bytes, L->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L->seg_done, 0, L->seg_bytes, L->stream);  // tickets start at 1
     if (e != cudaSuccess) {
         tclbm_destroy(L);
         return cuda_fail(e, "state clear");
@@ -695,6 +734,7 @@ tclbm_status tclbm_destroy(tclbm_lattice* L) {
     dev_free(L, L->usnap, L->usnap_bytes);
     dev_free(L, L->stage, L->stage_bytes);
     dev_free(L, L->err, 256);
+    dev_free(L, L->seg_done, L->seg_bytes);
     if (L->copy_event) cudaEventDestroy(L->copy_event);
     delete L;
     return TCLBM_OK;

@@ -44,6 +44,11 @@ struct tclbm_lattice {
     CUtensorMap maps[2];  // TMA descriptors of the two copies for box width of tx
     int maps_tx = 0;
     int* err = nullptr;  // device error word of the step kernels
+    // completion tickets of the TMA kernel's work items (chained launches) and the
+    // ticket of the last launch that published them
+    unsigned* seg_done = nullptr;
+    size_t seg_bytes = 0;
+    unsigned ticket = 0;
     char desc[256] = "";
     // CUDA graph of 2 * kGraphPairs step launches (parity preserved)
     cudaGraphExec_t graph = nullptr;

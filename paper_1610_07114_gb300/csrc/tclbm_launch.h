@@ -35,6 +35,13 @@ struct StepLaunch {
     const CUtensorMap* src_map;  // tensor map of the source copy (KERNEL_TMA)
     int* err;                    // device error word (bounded waits that expired)
     int parity;                  // index of the source copy (selects the step counter)
+    // chained TMA launches (tclbm_step_tma_corr): per-item completion tickets (nullptr:
+    // none), their capacity, this launch's ticket, and whether to wait for the previous
+    // launch's neighbouring items instead of its whole grid
+    unsigned* seg_done = nullptr;
+    long long seg_cap = 0;
+    unsigned ticket = 0;
+    int chain = 0;
 };
 
 cudaError_t launch_step_fp32(const StepLaunch& k, const DevParams& p, const void* src, void* dst, cudaStream_t s);

@@ -69,6 +69,10 @@ template <class K>
 static cudaError_t launch_tma(K kernel, int tx, size_t smem, long long resident, const StepLaunch& k, const DevParams& p,
                               const ST* in, ST* out, cudaStream_t s) {
     const SegPlan plan = tma_seg_plan(p, tx, k.ty, resident);
+    // completion tickets only where every item has an entry
+    const long long items = (long long)((p.nx + tx - 1) / tx) * (plan.full + plan.half);
+    unsigned* seg_done = items <= k.seg_cap ? k.seg_done : nullptr;
+    const int chain = seg_done ? k.chain : 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)((p.nx + tx - 1) / tx), (unsigned)(plan.full + plan.half), 1);
     cfg.blockDim = dim3(tx, 1, 1);
@@ -79,7 +83,8 @@ static cudaError_t launch_tma(K kernel, int tx, size_t smem, long long resident,
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, p, *k.src_map, in, out, k.ty, plan.full, plan.extra, k.err);
+    return cudaLaunchKernelEx(&cfg, kernel, p, *k.src_map, in, out, k.ty, plan.full, plan.extra, k.err, seg_done,
+                              k.ticket, chain);
 }
 
 // CTAs of tclbm_step_tma_plain<TX, THERMAL> the current device holds resident at once

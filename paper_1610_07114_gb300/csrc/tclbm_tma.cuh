@@ -298,7 +298,8 @@ template <int TX, bool THERMAL, class ST>
 __global__ void __launch_bounds__(TX, 512 / TX) tclbm_step_tma_plain(const __grid_constant__ DevParams p, const __grid_constant__ CUtensorMap map,
                                                            const ST* __restrict__ src, ST* __restrict__ dst,
                                                            int rows_per_cta, int seg_full, int seg_extra,
-                                                           int* __restrict__ err) {
+                                                           int* __restrict__ err, unsigned* __restrict__ /*seg_done*/,
+                                                           unsigned /*ticket*/, int /*chain*/) {
     extern __shared__ __align__(128) unsigned char smem[];
     using RR = RowRing<TX, THERMAL, ST>;
     RR R;
@@ -502,20 +503,102 @@ __device__ __forceinline__ bool tma_corr_strip(const DevParams& p, const CUtenso
     return true;
 }
 
+// ---------------------------------------------------------------- chained launches
+//
+// Consecutive launches of the kernel below on one lattice can be chained: instead of
+// waiting for the whole previous grid (griddepcontrol.wait), a CTA waits only for the
+// nine work items around its own (strip +-1, segment +-1, wrapped on periodic axes) to
+// have finished the previous step.  Those items wrote every source row this CTA reads
+// (rows y0-3 .. y1+1, columns x0-M .. x0+TX+M, segments of at least 8 rows) and were the
+// only readers of the rows it overwrites, so the wait covers both orders.  Each item
+// publishes, once all its stores are issued, the launch's ticket (a per-lattice counter
+// that only grows) in seg_done[blockIdx.y * gridDim.x + blockIdx.x]; the next launch
+// (ticket + 1) proceeds once the nine entries reach ticket.  The next grid is released
+// when every CTA of this one has started (griddepcontrol.launch_dependents at entry), so
+// every item waited on is already resident or finished: the waits cannot deadlock.  The
+// first launch of a chain, and every launch of a captured graph, waits for the previous
+// grid as before.
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Every thread: true once the nine items around this CTA's reached `need` (false after
+// the error word was set, by this wait expiring (code 2) or by another CTA).
+__device__ __forceinline__ bool seg_wait_neighbours(const DevParams& p, const unsigned* __restrict__ seg_done,
+                                                    unsigned need, int* __restrict__ err) {
+    int fail = 0;
+    const int t = threadIdx.x;
+    if (t < 9) {
+        const int gx = (int)gridDim.x, gy = (int)gridDim.y;
+        int ix = (int)blockIdx.x + t % 3 - 1, iy = (int)blockIdx.y + t / 3 - 1;
+        bool use = true;
+        if (ix < 0 || ix >= gx) {
+            if (p.xper) ix = ix < 0 ? ix + gx : ix - gx;
+            else use = false;
+        }
+        if (iy < 0 || iy >= gy) {
+            if (p.yper) iy = iy < 0 ? iy + gy : iy - gy;
+            else use = false;
+        }
+        if (use) {
+            const unsigned* f = seg_done + (size_t)iy * gx + ix;
+            if ((int)(ld_acquire_gpu(f) - need) < 0) {
+                const long long deadline = globaltimer_ns() + kWaitNs;
+                while ((int)(ld_acquire_gpu(f) - need) < 0) {
+                    if (*(volatile int*)err) {
+                        fail = 1;
+                        break;
+                    }
+                    if (globaltimer_ns() > deadline) {
+                        atomicExch(err, 2);
+                        fail = 1;
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+            }
+        }
+    }
+    fail = __syncthreads_or(fail);
+    // the rows the neighbours stored through the generic proxy are read next by TMA
+    if (!fail) asm volatile("fence.proxy.async.global;" ::: "memory");
+    return !fail;
+}
+
+// Every thread, after its last store: publish this item's completion of launch `ticket`
+// (the release store is cumulative over the stores the barrier ordered before it).
+__device__ __forceinline__ void seg_mark_done(unsigned* __restrict__ seg_done, unsigned ticket) {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0)
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(seg_done + (size_t)blockIdx.y * gridDim.x + blockIdx.x),
+                     "r"(ticket)
+                     : "memory");
+}
+
+// seg_done: completion tickets of the work items (nullptr: none published); chain: wait
+// for the neighbouring items of launch ticket - 1 instead of the whole previous grid.
 template <int TX, class ST>
 __global__ void __launch_bounds__(TX, CorrShape<ST>::kThreadsPerSM / TX) tclbm_step_tma_corr(const __grid_constant__ DevParams p, const __grid_constant__ CUtensorMap map,
                                                           const ST* __restrict__ src, ST* __restrict__ dst,
                                                           int rows_per_cta, int seg_full, int seg_extra,
-                                                          int* __restrict__ err) {
+                                                          int* __restrict__ err, unsigned* __restrict__ seg_done,
+                                                          unsigned ticket, int chain) {
     extern __shared__ __align__(128) unsigned char smem[];
     // programmatic dependent launch: this grid's CTAs take the slots the previous step's
-    // grid frees and wait here for its completion (its writes are this step's source)
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // grid frees and wait here for its completion (its writes are this step's source),
+    // or, chained, for the previous step's items around their own
+    if (!chain) asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (*(volatile int*)err) return;  // an earlier launch gave up: do not queue more waits
     int y0, y1;
     tma_segment(p, rows_per_cta, seg_full, seg_extra, y0, y1);
+    if (chain && !seg_wait_neighbours(p, seg_done, ticket - 1u, err)) return;
     if (!tma_corr_strip<TX, ST>(p, &map, src, dst, blockIdx.x * TX, y0, y1, err, smem)) return;
+    if (seg_done) seg_mark_done(seg_done, ticket);
     if (blockIdx.x == 0 && blockIdx.y == 0) bump_step_counter(p);
 }
 

@@ -54,6 +54,34 @@ def test_expired_pipeline_wait_is_reported_and_the_context_recovers(T):
     assert np.array_equal(f, f_ref) and np.array_equal(h, h_ref)
 
 
+def test_expired_wait_in_a_chain_of_launches_is_reported_and_the_context_recovers(T):
+    # three chained launches: the first one's CTA for row 30 never gets that row and
+    # gives up after 1 s; the items of the next launches that wait for it see the error
+    # word and return instead of waiting out their own limit
+    case, fields = W.rayleigh_benard(1024, 512, Ra=1e4, seed=9)
+    ref = T.Lattice(case, fields)
+    ref.set_kernel(0)
+    ref.set_tile(128, 16)
+    ref.step(5)
+    f_ref, h_ref = ref.populations()
+    ref.close()
+
+    lat = T.Lattice(case, fields)
+    lat.set_kernel(0)
+    lat.set_tile(128, 16)
+    T.tclbm_test_skip_row(lat.handle, 30)
+    lat.step(3)
+    with pytest.raises(T.TclbmError) as err:
+        lat.diagnostics()
+    assert err.value.status == T.ETIMEOUT
+    T.tclbm_test_skip_row(lat.handle, -1)
+    lat.init_fields(fields)
+    lat.step(5)
+    f, h = lat.populations()
+    lat.close()
+    assert np.array_equal(f, f_ref) and np.array_equal(h, h_ref)
+
+
 def test_allocator_returning_null_gives_enomem(T):
     case, _ = W.random_periodic(64, 32, seed=1)
     params = T.params_from_case(case)

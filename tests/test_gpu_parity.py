@@ -226,6 +226,44 @@ def test_tma_rows_per_cta_are_bit_identical(T):
         assert np.array_equal(f, states[0][0]) and np.array_equal(h, states[0][1])
 
 
+@pytest.mark.parametrize("name,make,tile", [
+    # walls in y, 16-row segments with the half-height last wave (more than two waves)
+    ("rb_2048x1024_rows16", lambda: W.rayleigh_benard(2048, 1024, seed=5), (128, 16)),
+    # a last strip of 104 columns, 32-row segments
+    ("rb_1000x512_rows32", lambda: W.rayleigh_benard(1000, 512, seed=8), (128, 32)),
+    # periodic in x and y: the neighbouring items of edge strips and segments wrap
+    ("periodic_1024x1024_rows8", lambda: W.random_periodic(1024, 1024, seed=9, force="accel"), (64, 8)),
+    # walls in x, periodic in y
+    ("xwalls_768x1024_rows16", lambda: W.with_walls(*W.random_periodic(768, 1024, seed=10, force="accel"),
+                                                    axis="x", kind="zouhe"), (128, 16)),
+    # 16-bit storage with round-to-nearest
+    ("rb_2048x1024_fp16_nearest", lambda: W.rayleigh_benard(2048, 1024, seed=5, storage="fp16"), (128, 32)),
+], ids=["rb_2048x1024_rows16", "rb_1000x512_rows32", "periodic_1024x1024_rows8", "xwalls_768x1024_rows16",
+        "rb_2048x1024_fp16_nearest"])
+def test_chained_tma_launches_equal_whole_grid_waits(T, name, make, tile):
+    # One call of 24 steps chains its launches (each work item waits for the nine items
+    # around it in the previous launch); 24 calls of one step wait for the whole previous
+    # grid every time.  The arithmetic is the same, so the states agree bit for bit.
+    case, fields = make()
+    if case.get("storage", "fp32") != "fp32":
+        case = dict(case, rounding="nearest")
+    states = []
+    for chained in (False, True):
+        lat = T.Lattice(case, fields)
+        lat.set_kernel(0)
+        lat.set_tile(*tile)
+        assert "tclbm_step_tma_corr" in lat.describe(), lat.describe()
+        if chained:
+            lat.step(24)
+        else:
+            for _ in range(24):
+                lat.step(1)
+        states.append(lat.populations())
+        lat.close()
+    (fa, ha), (fb, hb) = states
+    assert np.array_equal(fa, fb) and np.array_equal(ha, hb)
+
+
 @pytest.mark.parametrize("name,make", [
     ("athermal_taylor_green_2048", lambda: W.taylor_green(2048, F0=1e-8, nu=0.02)),
     ("thermal_no_correction_2048x1024", lambda: W.random_periodic(2048, 1024, seed=31, force="accel",

@@ -307,7 +307,7 @@ tclbm_status tclbm_batch_tma_shape(const tclbm_batch* batch, int32_t* tx, int32_
 
 /* Time every shape (tx in {32, 64, 128}, rows in {1, 2, 4, ..., 64} up to the tallest
  * lattice, persistent or not), then with the fastest of those every TMA-fed shape (tx
- * in {64, 128}, rows in {8, 16, 32}) where the batch has lattices for it, over
+ * in {64, 128}, rows in {8, 16, 32, 48, 64}) where the batch has lattices for it, over
  * `trial_steps` (>= 2, rounded up to even) steps each; keep the fastest combination and
  * report the direct-load shape through the non-NULL out pointers (best_us: device
  * microseconds per batch step; the TMA-fed shape through tclbm_batch_tma_shape).  The

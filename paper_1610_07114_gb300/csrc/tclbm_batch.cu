@@ -541,10 +541,10 @@ tclbm_status tclbm_batch_autotune(tclbm_batch* B, int32_t trial_steps, int32_t* 
     // TMA-fed strips for the wide thermal lattices with the correction term, the others
     // on the best direct-load shape
     static const int kTmaTx[] = {64, 128};
-    static const int kTmaRows[] = {8, 16, 32};
+    static const int kTmaRows[] = {8, 16, 32, 48, 64};
     const int dtx = bt, drows = br, dpers = bp;
     for (int t = 0; t < 2 && any_tma && ce == cudaSuccess && st == TCLBM_OK; ++t)
-        for (int r = 0; r < 3 && ce == cudaSuccess && st == TCLBM_OK; ++r) {
+        for (int r = 0; r < 5 && ce == cudaSuccess && st == TCLBM_OK; ++r) {
             if (kTmaRows[r] > max_ny) continue;
             trial(dtx, drows, dpers, kTmaTx[t], kTmaRows[r]);
         }

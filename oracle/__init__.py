@@ -50,6 +50,7 @@ class OracleParams(ctypes.Structure):
         ("wall_rho", ctypes.c_double * 4), ("wall_ux", ctypes.c_double * 4),
         ("wall_uy", ctypes.c_double * 4), ("wall_T", ctypes.c_double * 4),
         ("work", ctypes.c_int32),
+        ("adiabatic_flux", ctypes.c_int32),
     ]
 
 
@@ -120,6 +121,11 @@ def params(case: dict) -> OracleParams:
         p.wall_therm[i] = THERM[w.get("therm", "fixed")]
         p.wall_rho[i], p.wall_ux[i], p.wall_uy[i], p.wall_T[i] = w["rho"], w["ux"], w["uy"], w["T"]
     p.work = 1 if case.get("work") else 0
+    # adiabatic walls: "zero_gradient" (T_w = T_f, both paths) or "zero_flux" (oracle-only study)
+    adiabatic = case.get("adiabatic", "zero_gradient")
+    if adiabatic not in ("zero_gradient", "zero_flux"):
+        raise ValueError(f"adiabatic must be 'zero_gradient' or 'zero_flux', not {adiabatic!r}")
+    p.adiabatic_flux = 1 if adiabatic == "zero_flux" else 0
     if case.get("w_equal"):
         # BGK limit of Section V.A: w2 = w3 = w4 = w1 with w1 fixed from the viscosity.
         if case["visc_law"] != "nu":

@@ -50,6 +50,13 @@
  *     q_a = W_a F.u (D2Q9 weights, zeroth moment F.u, first moment zero) with the factor
  *     (1 - w_h/2), and the energy moment carries half a step of it, rho E =
  *     sum h_bar + F.u / 2, as Eq. 20 does for the momentum.  Initial h_bar = h^eq - q/2.
+ *   - Adiabatic temperature walls (Section V.B names non-equilibrium extrapolation
+ *     without saying how an adiabatic wall picks its temperature): T_w = T_f, the
+ *     interior neighbour's temperature.  This zero-gradient choice is first order: at
+ *     a wall at rest beside a sheared layer the total-energy distribution carries the
+ *     flux mu u_f^2 / 2 of total enthalpy into the wall node each step and the rebuild
+ *     removes it.  A study option (adiabatic_flux) takes instead the temperature at
+ *     which conduction and viscous work across that link cancel.
  *   - Walls are "wet": the wall lies on the first/last node row (or column); the
  *     boundary scheme rebuilds that node's populations after streaming and the
  *     node then collides like any other.  Zou-He is written for transformed
@@ -101,6 +108,9 @@ typedef struct {
     double wall_rho[4], wall_ux[4], wall_uy[4], wall_T[4];
     int32_t work;        /* 1: the body force's power F.u as a source of total energy (an extension:
                             the paper's Eq. 22 has none) */
+    int32_t adiabatic_flux; /* adiabatic walls: 0 zero gradient, T_w = T_f (the reading both paths
+                               take); 1 zero total-energy flux across the first link (a study of
+                               that reading, oracle only: the CUDA path has no such option) */
 } oracle_params;
 
 typedef struct { double rho, ux, uy, T, Fx, Fy, ax, ay; } macro_t;
@@ -403,7 +413,16 @@ static void wall_rebuild(const oracle_params* p, int side, int x, int y, double 
     const double b = b_dof(p);
     macro_t mf;
     macro_of(p, ff, hf, x + nxv, y + nyv, &mf);
-    const double Tw = p->thermal ? (p->wall_therm[side] == THERM_ADIABATIC ? mf.T : p->wall_T[side]) : p->T0;
+    /* Adiabatic wall temperature.  Zero gradient: T_w = T_f.  Zero flux (study option):
+     * conduction -lambda dT and viscous work -u.sigma across the link between the wall
+     * node and x_f cancel when lambda (T_f - T_w) + mu (|u_f|^2 - |u_w|^2)/2 = 0, i.e.
+     * T_w = T_f + Pr (|u_f|^2 - |u_w|^2) / (2 c_p) with lambda = mu c_p / Pr. */
+    double T_adiabatic = mf.T;
+    if (p->adiabatic_flux) {
+        const double cp = p->R * (b + 2.0) / 2.0;
+        T_adiabatic += p->Pr * ((mf.ux * mf.ux + mf.uy * mf.uy) - (uwx * uwx + uwy * uwy)) / (2.0 * cp);
+    }
+    const double Tw = p->thermal ? (p->wall_therm[side] == THERM_ADIABATIC ? T_adiabatic : p->wall_T[side]) : p->T0;
 
     if (kind == WALL_ZOUHE) {
         /* Non-equilibrium bounce-back (Zou-He) for a tangentially moving wall,

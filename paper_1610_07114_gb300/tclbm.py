@@ -309,6 +309,8 @@ def params_from_case(case: dict) -> tclbm_params:
     p.T_ref = case.get("T_ref", case["T0"])
     p.rounding = ROUNDING[case.get("rounding", "nearest")]
     p.work = int(bool(case.get("work")))
+    if case.get("adiabatic", "zero_gradient") != "zero_gradient":
+        raise ValueError("the CUDA path's adiabatic walls are zero-gradient (T_w = T_f) only")
     return p
 
 

@@ -70,3 +70,14 @@ def test_state_bytes_counts_both_population_copies(T):
     assert T.tclbm_state_bytes(p) >= 2 * 18 * n_pitch * 4
     case["storage"] = "fp16"
     assert T.tclbm_state_bytes(T.params_from_case(case)) >= 2 * 18 * n_pitch * 2
+
+
+def test_zero_flux_adiabatic_walls_are_refused_by_the_cuda_path(T):
+    # the zero-flux adiabatic wall is a study option of the oracle only; a case asking for
+    # it must not run silently with the CUDA path's zero-gradient walls
+    from paper_1610_07114_gb300 import workloads as W
+
+    case, _ = W.couette_paper()
+    T.params_from_case(case)
+    with pytest.raises(ValueError):
+        T.params_from_case(dict(case, adiabatic="zero_flux"))

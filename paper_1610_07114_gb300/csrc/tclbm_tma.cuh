@@ -509,8 +509,10 @@ __device__ __forceinline__ bool tma_corr_strip(const DevParams& p, const CUtenso
 // waiting for the whole previous grid (griddepcontrol.wait), a CTA waits only for the
 // nine work items around its own (strip +-1, segment +-1, wrapped on periodic axes) to
 // have finished the previous step.  Those items wrote every source row this CTA reads
-// (rows y0-3 .. y1+1, columns x0-M .. x0+TX+M, segments of at least 8 rows) and were the
-// only readers of the rows it overwrites, so the wait covers both orders.  Each item
+// (rows y0-3 .. y1+1 and columns x0-M .. x0+TX+M, inside those items where every segment
+// has at least 4 rows and the last strip at least M columns: the host chains only such
+// plans) and were the only readers of the rows it overwrites, so the wait covers both
+// orders.  Each item
 // publishes, once all its stores are issued, the launch's ticket (a per-lattice counter
 // that only grows) in seg_done[blockIdx.y * gridDim.x + blockIdx.x]; the next launch
 // (ticket + 1) proceeds once the nine entries reach ticket.  The next grid is released
